@@ -1,0 +1,519 @@
+#!/usr/bin/env python3
+"""Benchmark of the pospopcnt CUDA path on GB300.
+
+Default workload (one JSON line on stdout): single-stream pospopcnt_u16 over
+n = 2^30 16-bit words (2 GiB) of uniform random bits, input resident in HBM;
+a step is one pospopcnt_u16 call (memset + one kernel).  The metric is GB/s
+of input counted (and its fraction of the measured HBM copy bandwidth).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload u16|u16_onehot|u16_sparse|u16_misaligned|u8|u32|sweep|batched]
+
+Timing: CUDA events on the launching stream, a barrier and a device
+synchronisation on both sides of the K timed steps, the maximum over ranks.
+The input (2 GiB) is larger than L2, so no flush is needed between steps.
+Under torchrun each rank counts its own 2 GiB input (weak scaling, no
+collective on the data path).  `e2e` times the host-buffer entry point
+(pinned host memory -> device copies inside the timed region).  The CPU
+baseline and the `--impl reference` arm time the scalar CPU oracle on the
+host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pospopcnt_u16 GB/s"
+UNIT = "GB/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+# ---------------------------------------------------------------------------
+# helpers
+
+def peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def csrc_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1911_02696_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        with open(os.path.join(d, name), "rb") as f:
+            h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_key: str, nbytes: int):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    e = rec.get(kernel_key)
+    if not e or e.get("csrc_hash") != csrc_hash():
+        return None
+    # scale by input bytes (traffic grows in proportion for a streaming scan)
+    return int(e["dram_bytes_per_launch"] * nbytes / e["input_bytes"])
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.marks = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self):
+        self.marks.append(time.time())
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.lines:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        t0, t1 = (self.marks[0], self.marks[-1]) if len(self.marks) >= 2 else (0, 1e30)
+        rows = [line for t, line in self.lines if t0 <= t <= t1 + 0.25]
+        in_region = len(rows)
+        if not rows:
+            rows = [line for _, line in self.lines]
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            f = [x.strip() for x in r.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm), "samples_in_timed_region": in_region,
+                "power_w_max": max(power) if power else None}
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (timing harness only; the data path has no collective)
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def dist_max(value: float, world: int, device=None) -> float:
+    """Maximum of a per-rank float over all ranks."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def whole_job_throughput(bytes_per_rank_step: int, steps: int, world: int, max_ms: float) -> float:
+    """GB/s of the whole job: every rank's bytes over the slowest rank's time."""
+    return bytes_per_rank_step * steps * world / (max_ms * 1e-3) / 1e9
+
+
+# ---------------------------------------------------------------------------
+# workloads
+
+def make_input(kind: str, seed: int, log2_words: int | None = None):
+    """(host words, width, start offset in bytes, description)."""
+    import synth
+    if log2_words is not None:  # a smaller case of the same workload (profiling)
+        width = {"u8": 8, "u32": 32}.get(kind, 16)
+        return (synth.uniform_bits(seed, 1 << log2_words, width), width, 0,
+                f"pospopcnt_u{width} n=2^{log2_words} uniform random bits")
+    if kind == "u16":
+        return synth.uniform_bits(seed, 1 << 30, 16), 16, 0, "pospopcnt_u16 n=2^30 uniform random bits (2 GiB)"
+    if kind == "u16_onehot":
+        return synth.one_hot(seed, 1 << 30, 16), 16, 0, "pospopcnt_u16 n=2^30 one-hot Zipf(1.1) (2 GiB)"
+    if kind == "u16_sparse":
+        return synth.sparse(seed, 1 << 30, 16), 16, 0, "pospopcnt_u16 n=2^30 sparse Bernoulli(0.01) (2 GiB)"
+    if kind == "u16_misaligned":
+        return (synth.uniform_bits(seed, (1 << 30) + 7, 16), 16, 2,
+                "pospopcnt_u16 n=2^30+7 uniform bits, start 2 bytes past a 256-byte boundary")
+    if kind == "u8":
+        return synth.uniform_bits(seed, 1 << 31, 8), 8, 0, "pospopcnt_u8 n=2^31 uniform random bits (2 GiB)"
+    if kind == "u32":
+        return synth.uniform_bits(seed, 1 << 29, 32), 32, 0, "pospopcnt_u32 n=2^29 uniform random bits (2 GiB)"
+    raise ValueError(kind)
+
+
+def cpu_baseline(words, width, budget_s=8.0):
+    """The oracle as it stands, all host cores, on a bounded sample of the
+    same input: 2^26-word chunks until budget_s of wall time has passed."""
+    import oracle
+    cores = os.cpu_count() or 1
+    chunk = 1 << 26
+    done, t0, used = 0, time.perf_counter(), 1
+    while done < words.size:
+        _, used = oracle.pospopcnt_mt(words[done: done + chunk], width, cores)
+        done += min(chunk, words.size - done)
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    nbytes = done * (width // 8)
+    return {"value": round(nbytes / dt / 1e9, 4), "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": f"first {done} of {words.size} words ({nbytes / 2**20:.0f} MiB) of the same input, "
+                      f"{dt:.1f} s wall on {used} threads"}
+
+
+def run_plain(args, world, rank, local):
+    import torch
+    import paper_1911_02696_gb300 as ppc
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    words, width, offset, desc = make_input(args.workload, seed=rank, log2_words=args.log2_words)
+    nbytes = words.size * (width // 8)
+    host = torch.from_numpy(words.view(np.uint8))
+    buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+    x = buf[offset: offset + nbytes]
+    x.copy_(host)
+    counts = torch.empty(width, dtype=torch.int64, device=dev)
+    ppc.pospopcnt_init(local)
+    fn = {8: ppc.pospopcnt_u8, 16: ppc.pospopcnt_u16, 32: ppc.pospopcnt_u32}[width]
+    stream = torch.cuda.current_stream(dev)
+
+    # correctness of the timed configuration (oracle on rank 0's host copy is
+    # done by the tests; here a cheap invariant: the popcount total)
+    fn(x, counts=counts)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.6)
+    for _ in range(args.warmup):
+        fn(x, counts=counts)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    launches0 = ppc.pospopcnt_launch_count()
+    dist_barrier(world)
+    torch.cuda.synchronize()
+    clocks.mark()
+    ev[0].record(stream)
+    for i in range(args.steps):
+        fn(x, counts=counts)
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    clocks.mark()
+    dist_barrier(world)
+    launches = ppc.pospopcnt_launch_count() - launches0
+    time.sleep(0.3)
+    clocks.stop()
+    total_ms = ev[0].elapsed_time(ev[-1])
+    per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    max_ms = dist_max(total_ms, world, device=dev if world > 1 else None)
+    value = whole_job_throughput(nbytes, args.steps, world, max_ms)
+
+    # end to end through the host-buffer entry point
+    e2e = None
+    if not args.no_e2e:
+        pinned = host.pin_memory()
+        ppc.pospopcnt_count_host(width, pinned)  # allocates staging once
+        k_e2e = max(1, min(args.steps, args.e2e_steps))
+        dist_barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            ppc.pospopcnt_count_host(width, pinned)
+        e2e_s = dist_max(time.perf_counter() - t0, world, device=dev if world > 1 else None)
+        e2e = {"value": round(nbytes * k_e2e * world / e2e_s / 1e9, 3), "unit": UNIT,
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": width * 8, "steps": k_e2e}
+
+    peak, peak_src = peak_hbm()
+    launch_ms = statistics.mean(per_step)
+    achieved = (nbytes + width * 8) / (launch_ms * 1e-3) / 1e9
+    cfg = ppc.pospopcnt_get_config(width, words.size)
+    kname = {1: "csa", 2: "tma", 3: "ballot"}[cfg["kernel"]]
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_source": f"{peak_src} (copy bandwidth)",
+                "traffic": profiled_traffic(f"{kname}_u{width}", nbytes),
+                "kernel": f"{kname}_kernel<{width}> (+ a {width * 8}-byte memset)"}
+    out = None
+    if rank == 0:
+        out = {
+            "metric": METRIC if width == 16 else f"pospopcnt_u{width} GB/s", "value": round(value, 2),
+            "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(max_ms / args.steps, 5), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": f"u{width}", "data": "synthetic (seeded SplitMix64 on the host)",
+            "config": {"workload": desc, "n_words": int(words.size), "width": width, "start_offset_bytes": offset,
+                       "bytes_per_rank_step": nbytes, "launch_config": cfg, "parallelism": f"replicas x{world}",
+                       "l2": f"input {nbytes / 2**20:.0f} MiB vs L2 126 MB: "
+                             + ("no flush needed" if nbytes > (256 << 20) else "L2-resident (profiling case)")},
+            "words_per_s": round(value * 1e9 / (width // 8), 1),
+            "pct_hbm_peak": round(100 * value / world / peak, 2),
+            "roofline": roofline,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clocks.summary(),
+        }
+        if not args.no_cpu_baseline and world == 1:
+            out["cpu_baseline"] = cpu_baseline(words, width)
+    return out
+
+
+def run_sweep(args, world, rank, local):
+    """u16 input-size sweep 1 KiB .. 4 GiB in powers of 4; inputs at or
+    below the L2 size are reported warm (repeated) and cold (L2 flushed by
+    a 256 MiB write between steps)."""
+    import torch
+    import paper_1911_02696_gb300 as ppc
+    import synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ppc.pospopcnt_init(local)
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    counts = torch.empty(16, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    points = []
+    big = torch.from_numpy(synth.uniform_bytes(rank, 4 << 30)).to(dev)
+    for e in range(5, 17):
+        nbytes = 1 << (2 * e)
+        x = big[:nbytes]
+        reps = max(3, min(args.steps, int(2e9 // nbytes) + 3))
+        for _ in range(args.warmup):
+            ppc.pospopcnt_u16(x, counts=counts)
+        res = {"bytes": nbytes}
+        modes = ["warm", "cold"] if nbytes <= l2 else ["cold"]
+        for mode in modes:
+            ts = []
+            for _ in range(reps):
+                if mode == "cold" and nbytes <= l2:
+                    flush.fill_(1)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                ppc.pospopcnt_u16(x, counts=counts)
+                b.record(stream)
+                b.synchronize()
+                ts.append(a.elapsed_time(b))
+            med = statistics.median(ts)
+            res[mode] = {"median_us": round(med * 1e3, 2), "min_us": round(min(ts) * 1e3, 2),
+                         "GBps": round(nbytes / (med * 1e-3) / 1e9, 2)}
+        points.append(res)
+    if rank != 0:
+        return None
+    return {"metric": "pospopcnt_u16 GB/s vs input size", "value": points[-1]["cold"]["GBps"], "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+            "config": {"workload": "u16 size sweep 1 KiB..4 GiB, powers of 4", "l2_bytes": l2},
+            "points": points}
+
+
+def run_batched(args, world, rank, local):
+    """20,000 segments, lengths log-uniform in [1, 2^20] words, one-hot
+    rotated Zipf(1.1) per segment: one batched launch (replayed from a CUDA
+    graph) vs 20,000 plain pospopcnt_u16 launches on one stream."""
+    import torch
+    import paper_1911_02696_gb300 as ppc
+    import synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ppc.pospopcnt_init(local)
+    nseg = 20000
+    lens = synth.log_uniform_lengths(rank, nseg)
+    off = synth.offsets_from_lengths(lens)
+    words = synth.segmented_one_hot(rank, off, 16)
+    x = torch.from_numpy(words.view(np.uint8)).to(dev)
+    d_off = torch.from_numpy(off).to(dev)
+    out = torch.empty((nseg, 16), dtype=torch.int64, device=dev)
+    s = torch.cuda.Stream(dev)
+    s.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(s):
+        for _ in range(max(args.warmup, 1)):
+            ppc.pospopcnt_batched(x, d_off, 16, counts=out, stream=s)
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        ppc.pospopcnt_batched(x, d_off, 16, counts=out, stream=s)
+    for _ in range(args.warmup):
+        g.replay()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = max(1, min(args.steps, 50))
+    cur = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize()
+    a.record(cur)
+    for _ in range(steps):
+        g.replay()
+    b.record(cur)
+    torch.cuda.synchronize()
+    batched_ms = a.elapsed_time(b) / steps
+    got = out.cpu().numpy().view(np.uint64)
+    assert np.array_equal(got.sum(axis=1), lens.astype(np.uint64)), "one-hot row sums"
+    # 20,000 plain launches on one stream, same data: from the native host
+    # loop, and replayed from a CUDA graph that captured that loop
+    plain_out = torch.empty((nseg, 16), dtype=torch.int64, device=dev)
+    with torch.cuda.stream(s):
+        ppc.pospopcnt_plain_segments(x, off, 16, counts=plain_out, stream=s)
+    s.synchronize()
+    a.record(s)
+    with torch.cuda.stream(s):
+        ppc.pospopcnt_plain_segments(x, off, 16, counts=plain_out, stream=s)
+    b.record(s)
+    torch.cuda.synchronize()
+    plain_ms = a.elapsed_time(b)
+    assert np.array_equal(plain_out.cpu().numpy().view(np.uint64), got), "plain vs batched"
+    g2 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g2, stream=s):
+        ppc.pospopcnt_plain_segments(x, off, 16, counts=plain_out, stream=s)
+    g2.replay()
+    torch.cuda.synchronize()
+    a.record(cur)
+    g2.replay()
+    b.record(cur)
+    torch.cuda.synchronize()
+    plain_graph_ms = a.elapsed_time(b)
+    total = int(off[-1]) * 2
+    if rank != 0:
+        return None
+    return {"metric": "batched segments/s", "value": round(nseg / (batched_ms * 1e-3), 1), "unit": "segments/s",
+            "n_gpus": world, "steps": steps, "warmup": args.warmup, "ms_per_step": round(batched_ms, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
+            "data": "synthetic", "config": {"workload": "20,000 segments log-uniform [1, 2^20] words, one-hot "
+                                                        "rotated Zipf(1.1), one graph-replayed batched launch",
+                                            "total_bytes": total},
+            "batched_GBps": round(total / (batched_ms * 1e-3) / 1e9, 1),
+            "plain_launches": {"ms": round(plain_ms, 3), "segments_per_s": round(nseg / (plain_ms * 1e-3), 1),
+                               "graph_ms": round(plain_graph_ms, 3),
+                               "graph_segments_per_s": round(nseg / (plain_graph_ms * 1e-3), 1)},
+            "speedup_vs_plain": round(plain_ms / batched_ms, 2)}
+
+
+def run_reference(args, world, rank):
+    """The reference arm: the scalar CPU oracle on the host cores, each step
+    a bounded 2^26-word sample of the same workload."""
+    if rank != 0:
+        return None
+    import oracle
+    import synth
+    width = {"u8": 8, "u32": 32}.get(args.workload, 16)
+    words = synth.uniform_bits(0, (1 << 27) // (width // 8), width)
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle.pospopcnt_mt(words, width, cores)
+    t0 = time.perf_counter()
+    used = 1
+    for _ in range(args.steps):
+        _, used = oracle.pospopcnt_mt(words, width, cores)
+    dt = time.perf_counter() - t0
+    nbytes = words.size * (width // 8)
+    value = nbytes * args.steps / dt / 1e9
+    return {"impl": "reference", "metric": METRIC if width == 16 else f"pospopcnt_u{width} GB/s",
+            "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt * 1e3 / args.steps, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": f"u{width}", "data": "synthetic",
+            "config": {"workload": f"u{width} uniform random bits, CPU oracle sample of {nbytes >> 20} MiB per step"},
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": used, "kind": "oracle",
+                             "sample": f"{words.size} words ({nbytes >> 20} MiB) per step"},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+
+
+def main(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="u16",
+                   choices=["u16", "u16_onehot", "u16_sparse", "u16_misaligned", "u8", "u32", "sweep", "batched"])
+    p.add_argument("--e2e-steps", type=int, default=10)
+    p.add_argument("--log2-words", type=int, default=None,
+                   help="run a smaller uniform-bits case of 2^k words (profiling only)")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    args = p.parse_args(argv)
+    if args.warmup < 3:
+        p.error("--warmup must be >= 3")
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, world, rank)
+    else:
+        import torch
+        if world > 1:
+            torch.cuda.set_device(local)
+            dist_init(world, "nccl")
+        if args.workload == "sweep":
+            out = run_sweep(args, world, rank, local)
+        elif args.workload == "batched":
+            out = run_batched(args, world, rank, local)
+        else:
+            out = run_plain(args, world, rank, local)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            dist.destroy_process_group()
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,181 @@
+/*
+ * pospopcnt for GB300 (sm_103a) -- public C ABI.
+ *
+ * The positional population count of Klarqvist, Mula and Lemire, "Efficient
+ * Computation of Positional Population Counts Using SIMD Instructions"
+ * (arXiv 1911.02696): given a stream of k-bit words w_0..w_{n-1}, return the
+ * k sums counts[p] = sum_i ((w_i >> p) & 1), p = 0..k-1 (Abstract; §1; the
+ * scalar shift-mask-add routine of §4, Fig. 6).  For one-hot words the
+ * counts are the frequency histogram (§1, Table 1).
+ *
+ * Conventions shared by every entry point
+ *   - Words are little-endian; bit p of a word is (w >> p) & 1, so
+ *     counts[0] belongs to the least significant bit.
+ *   - n counts WORDS, not bytes.  Offsets are in words relative to d_in.
+ *   - d_in must be aligned to the word size (1, 2 or 4 bytes); any such
+ *     start is valid: words before the first 16-byte boundary and after the
+ *     last whole 16-byte vector are counted one by one (§4.1 counts the
+ *     residual that does not fill a SIMD block with the scalar routine).
+ *   - Results overwrite d_counts (the paper's routine adds into its
+ *     counters; the *_accumulate entry point keeps that form).  Counts are
+ *     exact uint64 values; every result is bit-exact.
+ *   - Entry points taking a cudaStream_t are asynchronous on that stream:
+ *     they enqueue a memset and one kernel, copy nothing between host and
+ *     device and never synchronise.  The caller owns every buffer; the
+ *     library never frees, retains or writes d_in.
+ *   - The first call on a device allocates the library's per-device
+ *     workspace (error word, work-queue slots); pospopcnt_init() does that
+ *     up front, after which the asynchronous calls allocate nothing.
+ *   - Errors are returned as pospopcnt_status values before anything is
+ *     enqueued; a failing CUDA call yields POSPOPCNT_ERR_CUDA and its
+ *     cudaError_t is kept for pospopcnt_last_cuda_error().
+ */
+#ifndef POSPOPCNT_GB300_H
+#define POSPOPCNT_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  POSPOPCNT_OK = 0,
+  POSPOPCNT_ERR_INVALID = 1,         /* null pointer with n > 0, bad width, bad config */
+  POSPOPCNT_ERR_MISALIGNED = 2,      /* d_in not aligned to the word size */
+  POSPOPCNT_ERR_CUDA = 3,            /* a CUDA runtime call failed */
+  POSPOPCNT_ERR_NOT_INITIALIZED = 4, /* no CUDA device / library state */
+  POSPOPCNT_ERR_TIMEOUT = 5,         /* a bounded device-side wait gave up */
+  POSPOPCNT_ERR_TOO_LARGE = 6        /* a size beyond a documented limit */
+} pospopcnt_status;
+
+/* Kernel families for the single-stream count (pospopcnt_count). */
+typedef enum {
+  POSPOPCNT_KERNEL_AUTO = 0,   /* the tuned choice for this width and size */
+  POSPOPCNT_KERNEL_CSA = 1,    /* 128-bit loads + per-thread carry-save circuit + popc flush */
+  POSPOPCNT_KERNEL_TMA = 2,    /* bulk async copies into an mbarrier ring, same circuit */
+  POSPOPCNT_KERNEL_BALLOT = 3  /* __ballot_sync bit transpose + popc (comparison kernel) */
+} pospopcnt_kernel;
+
+/* Launch configuration of the single-stream count. Zero fields take the
+ * library default.  threads: CTA size for CSA/BALLOT (128, 256 or 512);
+ * unroll: 16-byte vectors per thread per loop trip for CSA (2, 4 or 8; the
+ * carry-save circuit then spans 4*unroll 32-bit registers) and BALLOT
+ * (1, 2 or 4); blocks_per_sm: resident CTAs per SM the grid is sized for;
+ * stages / chunk_bytes: ring depth and bytes per stage for TMA
+ * (chunk_bytes a multiple of 16384, stages*chunk_bytes <= 196608). */
+typedef struct {
+  int kernel;
+  int threads;
+  int unroll;
+  int blocks_per_sm;
+  int stages;
+  int chunk_bytes;
+} pospopcnt_config;
+
+/* Creates the per-device state of `device` (error word, queue slots, SM
+ * count).  Idempotent.  Makes `device` current only for the duration of
+ * the call. */
+int pospopcnt_init(int device);
+
+/* pospopcnt over n 8-, 16- or 32-bit words at d_in (device memory); writes
+ * 8, 16 or 32 uint64 counts to d_counts (device memory, 8-byte aligned).
+ * The definition is that of the Abstract and §4 (Fig. 6); the method is
+ * the carry-save (Harley-Seal) circuit of §2-§4.1 run per GPU thread over
+ * 32-bit registers, flushed with popc.  n == 0 writes zero counts. */
+int pospopcnt_u8(const void* d_in, size_t n, uint64_t* d_counts, cudaStream_t stream);
+int pospopcnt_u16(const void* d_in, size_t n, uint64_t* d_counts, cudaStream_t stream);
+int pospopcnt_u32(const void* d_in, size_t n, uint64_t* d_counts, cudaStream_t stream);
+
+/* The same for width 8, 16 or 32 with an explicit kernel family
+ * (pospopcnt_kernel). */
+int pospopcnt_count(int width, int kernel, const void* d_in, size_t n, uint64_t* d_counts,
+                    cudaStream_t stream);
+
+/* The same with an explicit launch configuration (validated; see
+ * pospopcnt_config). */
+int pospopcnt_count_config(int width, const pospopcnt_config* cfg, const void* d_in, size_t n,
+                           uint64_t* d_counts, cudaStream_t stream);
+
+/* Accumulate form, the paper's convention (§4, Fig. 6 adds into its
+ * counters): d_counts[p] += counts[p].  Nothing is zeroed, so a stream can
+ * be counted in chunks over several calls. */
+int pospopcnt_count_accumulate(int width, const void* d_in, size_t n, uint64_t* d_counts,
+                               cudaStream_t stream);
+
+/* pospopcnt of HOST memory: copies h_in (n words, pinned or pageable) to the
+ * device in chunks through the library's staging buffers, overlapping the
+ * copies with counting on two streams, and writes the width uint64 counts to
+ * h_counts (host memory).  Synchronous: returns when h_counts is written.
+ * The first call on a device allocates the staging buffers
+ * (2 x 64 MiB) and two streams. */
+int pospopcnt_count_host(int width, const void* h_in, size_t n, uint64_t* h_counts);
+
+/* Segmented pospopcnt (one persistent launch over all segments).
+ * Segment s covers words [d_offsets[s], d_offsets[s+1]) of d_in; row s of
+ * d_counts (width uint64 values, row-major, nseg rows) receives its counts.
+ * d_offsets: nseg+1 int64 values in device memory, nondecreasing, >= 0
+ * (d_offsets[0] may be > 0; validity is the caller's contract).
+ * width: 8, 16 or 32 (bits).  nseg == 0 is a no-op.  Uses one of the
+ * device's queue slots, chosen per stream: launches on one stream never
+ * share a slot concurrently; a CUDA graph captured from a stream keeps that
+ * stream's slot and must not be replayed concurrently with itself or with
+ * batched calls on that stream. */
+int pospopcnt_batched(const void* d_in, const int64_t* d_offsets, size_t nseg, int width,
+                      uint64_t* d_counts, cudaStream_t stream);
+
+/* The per-segment alternative to pospopcnt_batched, for offsets known on
+ * the host: one plain count (memset + kernel) per segment, issued in order
+ * on `stream` from a host loop.  h_offsets: nseg+1 int64 word offsets in
+ * host memory; d_counts as for pospopcnt_batched.  Asynchronous. */
+int pospopcnt_plain_segments(const void* d_in, const int64_t* h_offsets, size_t nseg, int width,
+                             uint64_t* d_counts, cudaStream_t stream);
+
+/* Synchronises `stream`, reads and clears the device error word (set by a
+ * bounded wait that gave up).  Returns POSPOPCNT_OK or
+ * POSPOPCNT_ERR_TIMEOUT. */
+int pospopcnt_check_device_error(cudaStream_t stream);
+
+/* Host-only planning of the head/body/tail split (§4.1 residual handling):
+ * for n words of `width` bits starting at address addr, the words before the
+ * first 16-byte boundary (head), the whole 16-byte vectors (body) and the
+ * words after them (tail).  Touches no device. */
+int pospopcnt_plan_split(int width, uint64_t addr, size_t n, size_t* head_words,
+                         size_t* body_vectors, size_t* tail_words);
+
+/* The launch configuration the library uses for (width, n) on the current
+ * device, and a way to replace it for a size class (size_class =
+ * floor(log4(bytes)), 0..20; -1 = every class). */
+int pospopcnt_get_config(int width, size_t n, pospopcnt_config* cfg);
+int pospopcnt_set_config(int width, int size_class, const pospopcnt_config* cfg);
+
+/* Times every candidate configuration on the caller's device buffer d_in
+ * (n words) with CUDA events, installs the fastest for that width and size
+ * class, and returns it in best (and its time in *best_ms).  d_scratch_counts:
+ * device memory for width uint64 values.  Synchronous. */
+int pospopcnt_autotune(int width, const void* d_in, size_t n, uint64_t* d_scratch_counts,
+                       pospopcnt_config* best, float* best_ms);
+
+/* Self-test of the bounded-wait path used by the TMA ring: launches one warp
+ * that waits on an mbarrier no one will ever complete, gives up after
+ * limit_ns nanoseconds (at most 10^9), sets the device error word and
+ * returns normally.  pospopcnt_check_device_error(stream) then reports
+ * POSPOPCNT_ERR_TIMEOUT and clears the word.  Nothing faults or traps. */
+int pospopcnt_selftest_timeout(uint64_t limit_ns, cudaStream_t stream);
+
+/* Message for a status code, and the cudaError_t of the last CUDA failure
+ * seen by this thread. */
+const char* pospopcnt_strerror(int status);
+int pospopcnt_last_cuda_error(void);
+
+/* Number of kernels this library has launched in this process (all devices);
+ * lets a caller count launches inside a timed region. */
+uint64_t pospopcnt_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POSPOPCNT_GB300_H */

@@ -1,0 +1,329 @@
+"""pospopcnt on GB300: Python binding of the C ABI in include/pospopcnt.h.
+
+The positional population count (Klarqvist, Mula, Lemire, arXiv 1911.02696):
+for k-bit words w_i, counts[p] = sum_i ((w_i >> p) & 1), p = 0..k-1.
+
+Every function here has the name of a C entry point and only marshals
+arguments: tensors become device pointers and word counts, the stream
+becomes a cudaStream_t, and a non-zero status becomes a PospopcntError.
+All counting runs in the library's CUDA kernels; there is no CPU path.
+PyTorch supplies device memory and streams.  Counts are returned in int64
+tensors (the values are uint64 and never exceed 2^63 here).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+__all__ = [
+    "PospopcntError", "load", "pospopcnt_init", "pospopcnt_u8", "pospopcnt_u16", "pospopcnt_u32",
+    "pospopcnt_count", "pospopcnt_count_config", "pospopcnt_count_accumulate", "pospopcnt_count_host",
+    "pospopcnt_batched", "pospopcnt_plain_segments", "pospopcnt_check_device_error", "pospopcnt_plan_split",
+    "pospopcnt_get_config", "pospopcnt_set_config", "pospopcnt_autotune", "pospopcnt_strerror",
+    "pospopcnt_last_cuda_error", "pospopcnt_launch_count", "pospopcnt_selftest_timeout", "KERNELS",
+    "Config",
+]
+
+KERNELS = {"auto": 0, "csa": 1, "tma": 2, "ballot": 3}
+STATUS = {0: "OK", 1: "ERR_INVALID", 2: "ERR_MISALIGNED", 3: "ERR_CUDA", 4: "ERR_NOT_INITIALIZED",
+          5: "ERR_TIMEOUT", 6: "ERR_TOO_LARGE"}
+
+
+class PospopcntError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib().pospopcnt_strerror(status).decode()
+        extra = ""
+        if status == 3:
+            extra = f" (cudaError {_lib().pospopcnt_last_cuda_error()})"
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}{extra}")
+
+
+class Config(ctypes.Structure):
+    """pospopcnt_config: kernel, threads, unroll, blocks_per_sm, stages, chunk_bytes."""
+    _fields_ = [("kernel", ctypes.c_int), ("threads", ctypes.c_int), ("unroll", ctypes.c_int),
+                ("blocks_per_sm", ctypes.c_int), ("stages", ctypes.c_int), ("chunk_bytes", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_handle = None
+
+
+def load(build_if_needed: bool = True) -> ctypes.CDLL:
+    """Loads libpospopcnt_gb300.so (building it first if it is missing or
+    stale).  Raises if it cannot be built or loaded: there is no fallback."""
+    global _handle
+    with _lock:
+        if _handle is None:
+            path = _build.build() if build_if_needed else _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library not built: {path}")
+            lib = ctypes.CDLL(path)
+            _declare(lib)
+            _handle = lib
+    return _handle
+
+
+_lib = load
+
+
+def _declare(lib):
+    i32, u64, vp, sz = ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_size_t
+    P = ctypes.POINTER
+    sig = {
+        "pospopcnt_init": (i32, [i32]),
+        "pospopcnt_u8": (i32, [vp, sz, vp, vp]),
+        "pospopcnt_u16": (i32, [vp, sz, vp, vp]),
+        "pospopcnt_u32": (i32, [vp, sz, vp, vp]),
+        "pospopcnt_count": (i32, [i32, i32, vp, sz, vp, vp]),
+        "pospopcnt_count_config": (i32, [i32, P(Config), vp, sz, vp, vp]),
+        "pospopcnt_count_accumulate": (i32, [i32, vp, sz, vp, vp]),
+        "pospopcnt_count_host": (i32, [i32, vp, sz, vp]),
+        "pospopcnt_batched": (i32, [vp, vp, sz, i32, vp, vp]),
+        "pospopcnt_plain_segments": (i32, [vp, vp, sz, i32, vp, vp]),
+        "pospopcnt_check_device_error": (i32, [vp]),
+        "pospopcnt_plan_split": (i32, [i32, u64, sz, P(sz), P(sz), P(sz)]),
+        "pospopcnt_get_config": (i32, [i32, sz, P(Config)]),
+        "pospopcnt_set_config": (i32, [i32, i32, P(Config)]),
+        "pospopcnt_autotune": (i32, [i32, vp, sz, vp, P(Config), P(ctypes.c_float)]),
+        "pospopcnt_strerror": (ctypes.c_char_p, [i32]),
+        "pospopcnt_last_cuda_error": (i32, []),
+        "pospopcnt_launch_count": (u64, []),
+        "pospopcnt_selftest_timeout": (i32, [u64, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype, f.argtypes = res, args
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise PospopcntError(status, where)
+
+
+# ---------------------------------------------------------------------------
+# tensor marshalling
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream, device):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _words(x, width: int):
+    """(device pointer, word count) of a contiguous CUDA tensor viewed as
+    `width`-bit words."""
+    if not x.is_cuda:
+        raise ValueError("input must be a CUDA tensor (use pospopcnt_count_host for host memory)")
+    if not x.is_contiguous():
+        raise ValueError("input must be contiguous")
+    nbytes = x.numel() * x.element_size()
+    if nbytes % (width // 8):
+        raise ValueError(f"{nbytes} bytes is not a whole number of {width}-bit words")
+    return x.data_ptr(), nbytes // (width // 8)
+
+
+def _counts_out(counts, width: int, rows: int | None, device):
+    torch = _torch()
+    shape = (width,) if rows is None else (rows, width)
+    if counts is None:
+        return torch.empty(shape, dtype=torch.int64, device=device)
+    if counts.dtype not in (torch.int64, getattr(torch, "uint64", torch.int64)) or not counts.is_contiguous():
+        raise ValueError("counts must be a contiguous 64-bit integer tensor")
+    if counts.numel() != int(np.prod(shape)) or counts.device != device:
+        raise ValueError(f"counts must hold {shape} values on {device}")
+    return counts
+
+
+def pospopcnt_init(device: int = 0) -> None:
+    _check(_lib().pospopcnt_init(device), "pospopcnt_init")
+
+
+def _plain(name: str, width: int, x, counts, stream):
+    torch = _torch()
+    ptr, n = _words(x, width)
+    out = _counts_out(counts, width, None, x.device)
+    with torch.cuda.device(x.device):
+        _check(getattr(_lib(), name)(ptr, n, out.data_ptr(), _stream_handle(stream, x.device)), name)
+    return out
+
+
+def pospopcnt_u8(x, counts=None, stream=None):
+    """Counts of the 8-bit words of CUDA tensor x (int64[8])."""
+    return _plain("pospopcnt_u8", 8, x, counts, stream)
+
+
+def pospopcnt_u16(x, counts=None, stream=None):
+    """Counts of the 16-bit words of CUDA tensor x (int64[16])."""
+    return _plain("pospopcnt_u16", 16, x, counts, stream)
+
+
+def pospopcnt_u32(x, counts=None, stream=None):
+    """Counts of the 32-bit words of CUDA tensor x (int64[32])."""
+    return _plain("pospopcnt_u32", 32, x, counts, stream)
+
+
+def pospopcnt_count(width: int, x, kernel="auto", counts=None, stream=None):
+    torch = _torch()
+    ptr, n = _words(x, width)
+    out = _counts_out(counts, width, None, x.device)
+    k = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+    with torch.cuda.device(x.device):
+        _check(_lib().pospopcnt_count(width, k, ptr, n, out.data_ptr(), _stream_handle(stream, x.device)),
+               "pospopcnt_count")
+    return out
+
+
+def _make_config(cfg) -> Config:
+    if isinstance(cfg, Config):
+        return cfg
+    c = Config()
+    for k, v in dict(cfg).items():
+        setattr(c, k, KERNELS[v] if k == "kernel" and isinstance(v, str) else int(v))
+    return c
+
+
+def pospopcnt_count_config(width: int, cfg, x, counts=None, stream=None):
+    torch = _torch()
+    ptr, n = _words(x, width)
+    out = _counts_out(counts, width, None, x.device)
+    c = _make_config(cfg)
+    with torch.cuda.device(x.device):
+        _check(_lib().pospopcnt_count_config(width, ctypes.byref(c), ptr, n, out.data_ptr(),
+                                             _stream_handle(stream, x.device)), "pospopcnt_count_config")
+    return out
+
+
+def pospopcnt_count_accumulate(width: int, x, counts, stream=None):
+    """counts += pospopcnt(x) (the paper's accumulate convention)."""
+    torch = _torch()
+    ptr, n = _words(x, width)
+    out = _counts_out(counts, width, None, x.device)
+    with torch.cuda.device(x.device):
+        _check(_lib().pospopcnt_count_accumulate(width, ptr, n, out.data_ptr(),
+                                                 _stream_handle(stream, x.device)), "pospopcnt_count_accumulate")
+    return out
+
+
+def pospopcnt_count_host(width: int, h, out: np.ndarray | None = None) -> np.ndarray:
+    """Counts of host memory h (numpy array or CPU tensor; pinned memory is
+    fastest).  Synchronous; returns uint64[width]."""
+    if hasattr(h, "data_ptr"):
+        if h.is_cuda or not h.is_contiguous():
+            raise ValueError("h must be a contiguous host tensor")
+        ptr, nbytes = h.data_ptr(), h.numel() * h.element_size()
+    else:
+        a = np.ascontiguousarray(h)
+        ptr, nbytes = a.ctypes.data, a.nbytes
+    if nbytes % (width // 8):
+        raise ValueError("not a whole number of words")
+    if out is None:
+        out = np.zeros(width, dtype=np.uint64)
+    assert out.dtype == np.uint64 and out.size == width and out.flags.c_contiguous
+    _check(_lib().pospopcnt_count_host(width, ptr, nbytes // (width // 8), out.ctypes.data),
+           "pospopcnt_count_host")
+    return out
+
+
+def pospopcnt_batched(x, offsets, width: int, counts=None, stream=None):
+    """Row s = counts of words [offsets[s], offsets[s+1]) of x; offsets is a
+    CUDA int64 tensor of nseg+1 word offsets.  Returns int64[nseg, width]."""
+    torch = _torch()
+    ptr, _ = _words(x, width)
+    if offsets.dtype != torch.int64 or not offsets.is_cuda or not offsets.is_contiguous():
+        raise ValueError("offsets must be a contiguous CUDA int64 tensor")
+    nseg = max(offsets.numel() - 1, 0)
+    out = _counts_out(counts, width, nseg, x.device)
+    with torch.cuda.device(x.device):
+        _check(_lib().pospopcnt_batched(ptr, offsets.data_ptr(), nseg, width, out.data_ptr(),
+                                        _stream_handle(stream, x.device)), "pospopcnt_batched")
+    return out
+
+
+def pospopcnt_plain_segments(x, offsets: np.ndarray, width: int, counts=None, stream=None):
+    """One plain count per segment, issued from a host loop; offsets is a
+    host int64 array of nseg+1 word offsets.  Returns int64[nseg, width]."""
+    torch = _torch()
+    ptr, _ = _words(x, width)
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    nseg = max(off.size - 1, 0)
+    out = _counts_out(counts, width, nseg, x.device)
+    with torch.cuda.device(x.device):
+        _check(_lib().pospopcnt_plain_segments(ptr, off.ctypes.data, nseg, width, out.data_ptr(),
+                                               _stream_handle(stream, x.device)), "pospopcnt_plain_segments")
+    return out
+
+
+def pospopcnt_check_device_error(stream=None, device=None) -> int:
+    """Synchronises the stream and returns the device error status (0 = OK)."""
+    torch = _torch()
+    device = device if device is not None else torch.cuda.current_device()
+    with torch.cuda.device(device):
+        return int(_lib().pospopcnt_check_device_error(_stream_handle(stream, device)))
+
+
+def pospopcnt_plan_split(width: int, addr: int, n: int):
+    """(head_words, body_vectors, tail_words) for n words at address addr."""
+    h, b, t = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+    _check(_lib().pospopcnt_plan_split(width, addr, n, ctypes.byref(h), ctypes.byref(b), ctypes.byref(t)),
+           "pospopcnt_plan_split")
+    return h.value, b.value, t.value
+
+
+def pospopcnt_get_config(width: int, n: int) -> dict:
+    c = Config()
+    _check(_lib().pospopcnt_get_config(width, n, ctypes.byref(c)), "pospopcnt_get_config")
+    return c.as_dict()
+
+
+def pospopcnt_set_config(width: int, size_class: int, cfg) -> None:
+    c = _make_config(cfg)
+    _check(_lib().pospopcnt_set_config(width, size_class, ctypes.byref(c)), "pospopcnt_set_config")
+
+
+def pospopcnt_autotune(width: int, x, scratch_counts=None):
+    """Times the candidate configurations on x; installs and returns the best
+    (dict) and its time in ms."""
+    torch = _torch()
+    ptr, n = _words(x, width)
+    out = _counts_out(scratch_counts, width, None, x.device)
+    c, ms = Config(), ctypes.c_float()
+    with torch.cuda.device(x.device):
+        _check(_lib().pospopcnt_autotune(width, ptr, n, out.data_ptr(), ctypes.byref(c), ctypes.byref(ms)),
+               "pospopcnt_autotune")
+    return c.as_dict(), ms.value
+
+
+def pospopcnt_strerror(status: int) -> str:
+    return _lib().pospopcnt_strerror(status).decode()
+
+
+def pospopcnt_last_cuda_error() -> int:
+    return int(_lib().pospopcnt_last_cuda_error())
+
+
+def pospopcnt_launch_count() -> int:
+    return int(_lib().pospopcnt_launch_count())
+
+
+def pospopcnt_selftest_timeout(limit_ns: int = 1_000_000, stream=None, device=None) -> None:
+    """Runs the bounded-wait self-test kernel (see the C header)."""
+    torch = _torch()
+    device = device if device is not None else torch.cuda.current_device()
+    with torch.cuda.device(device):
+        _check(_lib().pospopcnt_selftest_timeout(limit_ns, _stream_handle(stream, device)),
+               "pospopcnt_selftest_timeout")

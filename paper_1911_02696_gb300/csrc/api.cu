@@ -1,0 +1,480 @@
+// The C ABI of include/pospopcnt.h: argument checks, per-device state,
+// launch configuration tables, the host-buffer path and the autotuner.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.h"
+#include "pospopcnt.h"
+
+namespace ppc {
+
+namespace {
+
+constexpr int MAX_DEVICES = 64;
+constexpr int NCLASSES = 21;  // floor(log4(bytes)) for bytes < 2^42
+
+std::mutex g_mutex;
+DeviceState g_state[MAX_DEVICES];
+std::unordered_map<cudaStream_t, int> g_slots[MAX_DEVICES];
+pospopcnt_config g_cfg[MAX_DEVICES][3][NCLASSES];
+bool g_cfg_ready[MAX_DEVICES] = {};
+std::mutex g_host_mutex[MAX_DEVICES];
+std::atomic<uint64_t> g_launches{0};
+thread_local int t_last_cuda = 0;
+
+int width_index(int width) { return width == 8 ? 0 : width == 16 ? 1 : width == 32 ? 2 : -1; }
+
+int size_class(uint64_t bytes) {
+  int c = 0;
+  while (c + 1 < NCLASSES && (uint64_t(1) << (2 * (c + 1))) <= bytes) ++c;
+  return c;
+}
+
+pospopcnt_config default_config() {
+  pospopcnt_config c;
+  c.kernel = POSPOPCNT_KERNEL_CSA;
+  c.threads = 256;
+  c.unroll = 4;
+  c.blocks_per_sm = 0;
+  c.stages = 4;
+  c.chunk_bytes = 32768;
+  return c;
+}
+
+void init_configs(int dev) {
+  if (g_cfg_ready[dev]) return;
+  for (int w = 0; w < 3; ++w)
+    for (int c = 0; c < NCLASSES; ++c) g_cfg[dev][w][c] = default_config();
+  g_cfg_ready[dev] = true;
+}
+
+int init_locked(int device) {
+  if (device < 0 || device >= MAX_DEVICES) return POSPOPCNT_ERR_INVALID;
+  DeviceState& st = g_state[device];
+  if (st.ready) return POSPOPCNT_OK;
+  int prev = -1;
+  cudaError_t e = cudaGetDevice(&prev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if ((e = cudaSetDevice(device)) != cudaSuccess) return cuda_fail(e);
+  int rc = POSPOPCNT_OK;
+  do {
+    if ((e = cudaDeviceGetAttribute(&st.sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) break;
+    if ((e = cudaDeviceGetAttribute(&st.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device)) !=
+        cudaSuccess)
+      break;
+    if ((e = cudaMalloc(reinterpret_cast<void**>(&st.d_err), 256)) != cudaSuccess) break;
+    if ((e = cudaMemset(st.d_err, 0, 256)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&st.d_queue, size_t(QUEUE_SLOTS) * QUEUE_SLOT_BYTES)) != cudaSuccess) break;
+    if ((e = cudaMemset(st.d_queue, 0, size_t(QUEUE_SLOTS) * QUEUE_SLOT_BYTES)) != cudaSuccess) break;
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) break;
+  } while (false);
+  if (e != cudaSuccess) rc = cuda_fail(e);
+  cudaSetDevice(prev);
+  if (rc == POSPOPCNT_OK) {
+    st.device = device;
+    init_configs(device);
+    st.ready = true;
+  }
+  return rc;
+}
+
+}  // namespace
+
+int cuda_fail(cudaError_t e) {
+  t_last_cuda = int(e);
+  return POSPOPCNT_ERR_CUDA;
+}
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+DeviceState* current_state(int* status) {
+  int dev = -1;
+  const cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    t_last_cuda = int(e);
+    *status = POSPOPCNT_ERR_NOT_INITIALIZED;
+    return nullptr;
+  }
+  if (dev < 0 || dev >= MAX_DEVICES) {
+    *status = POSPOPCNT_ERR_NOT_INITIALIZED;
+    return nullptr;
+  }
+  if (!g_state[dev].ready) {
+    std::lock_guard<std::mutex> lk(g_mutex);
+    const int rc = init_locked(dev);
+    if (rc != POSPOPCNT_OK) {
+      *status = rc;
+      return nullptr;
+    }
+  }
+  *status = POSPOPCNT_OK;
+  return &g_state[dev];
+}
+
+Split plan_split(int width, uint64_t addr, size_t n) {
+  const uint64_t wb = uint64_t(width / 8);
+  const uint64_t nbytes = uint64_t(n) * wb;
+  uint64_t head = (16 - (addr & 15)) & 15;
+  if (head > nbytes) head = nbytes;
+  head -= head % wb;  // addr is word aligned, so this is already whole words
+  const uint64_t body = (nbytes - head) / 16;
+  const uint64_t tail = nbytes - head - body * 16;
+  return Split{size_t(head / wb), size_t(body), size_t(tail / wb)};
+}
+
+int normalize_config(const DeviceState& st, int width, pospopcnt_config* c) {
+  if (width_index(width) < 0) return POSPOPCNT_ERR_INVALID;
+  const pospopcnt_config d = default_config();
+  if (c->kernel == POSPOPCNT_KERNEL_AUTO) c->kernel = d.kernel;
+  if (c->threads == 0) c->threads = 256;
+  if (c->blocks_per_sm < 0 || c->blocks_per_sm > 32) return POSPOPCNT_ERR_INVALID;
+  switch (c->kernel) {
+    case POSPOPCNT_KERNEL_CSA:
+      if (c->unroll == 0) c->unroll = 4;
+      if (c->threads != 128 && c->threads != 256 && c->threads != 512) return POSPOPCNT_ERR_INVALID;
+      if (c->unroll != 2 && c->unroll != 4 && c->unroll != 8) return POSPOPCNT_ERR_INVALID;
+      return POSPOPCNT_OK;
+    case POSPOPCNT_KERNEL_BALLOT:
+      if (c->unroll == 0) c->unroll = 2;
+      if (c->threads != 256) return POSPOPCNT_ERR_INVALID;
+      if (c->unroll != 1 && c->unroll != 2 && c->unroll != 4) return POSPOPCNT_ERR_INVALID;
+      return POSPOPCNT_OK;
+    case POSPOPCNT_KERNEL_TMA: {
+      if (c->stages == 0) c->stages = d.stages;
+      if (c->chunk_bytes == 0) c->chunk_bytes = d.chunk_bytes;
+      if (c->stages < 2 || c->stages > 16) return POSPOPCNT_ERR_INVALID;
+      if (c->chunk_bytes < 16384 || c->chunk_bytes % 16384 != 0 || c->chunk_bytes > 196608)
+        return POSPOPCNT_ERR_INVALID;
+      const long smem = long(c->stages) * long(c->chunk_bytes);
+      const long limit = st.smem_optin > 0 ? std::min<long>(st.smem_optin - 1024, 196608) : 196608;
+      if (smem > limit) return POSPOPCNT_ERR_INVALID;
+      return POSPOPCNT_OK;
+    }
+  }
+  return POSPOPCNT_ERR_INVALID;
+}
+
+template <int K>
+int launch_plain_k(const DeviceState&, const pospopcnt_config&, const void*, size_t, unsigned long long*,
+                   cudaStream_t);
+
+int launch_plain(const DeviceState& st, int width, const pospopcnt_config& cfg, const void* d_in, size_t n,
+                 unsigned long long* d_counts, cudaStream_t stream) {
+  switch (width) {
+    case 8: return launch_plain_k<8>(st, cfg, d_in, n, d_counts, stream);
+    case 16: return launch_plain_k<16>(st, cfg, d_in, n, d_counts, stream);
+    case 32: return launch_plain_k<32>(st, cfg, d_in, n, d_counts, stream);
+  }
+  return POSPOPCNT_ERR_INVALID;
+}
+
+namespace {
+
+int check_args(int width, const void* d_in, size_t n, const void* d_counts) {
+  if (width_index(width) < 0) return POSPOPCNT_ERR_INVALID;
+  if (!d_counts || (n > 0 && !d_in)) return POSPOPCNT_ERR_INVALID;
+  if (reinterpret_cast<uintptr_t>(d_counts) % 8 != 0) return POSPOPCNT_ERR_MISALIGNED;
+  if (reinterpret_cast<uintptr_t>(d_in) % uintptr_t(width / 8) != 0) return POSPOPCNT_ERR_MISALIGNED;
+  if (n > (size_t(1) << 42) / size_t(width / 8)) return POSPOPCNT_ERR_TOO_LARGE;
+  return POSPOPCNT_OK;
+}
+
+pospopcnt_config config_for(const DeviceState& st, int width, size_t n) {
+  return g_cfg[st.device][width_index(width)][size_class(uint64_t(n) * uint64_t(width / 8))];
+}
+
+int count_impl(int width, const pospopcnt_config* cfg_in, bool zero, const void* d_in, size_t n,
+               uint64_t* d_counts, cudaStream_t stream) {
+  int rc = check_args(width, d_in, n, d_counts);
+  if (rc != POSPOPCNT_OK) return rc;
+  DeviceState* st = current_state(&rc);
+  if (!st) return rc;
+  pospopcnt_config cfg = cfg_in ? *cfg_in : config_for(*st, width, n);
+  if ((rc = normalize_config(*st, width, &cfg)) != POSPOPCNT_OK) return rc;
+  if (zero) {
+    const cudaError_t e = cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * size_t(width), stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  if (n == 0) return POSPOPCNT_OK;
+  return launch_plain(*st, width, cfg, d_in, n, reinterpret_cast<unsigned long long*>(d_counts), stream);
+}
+
+}  // namespace
+
+}  // namespace ppc
+
+using namespace ppc;
+
+extern "C" {
+
+int pospopcnt_init(int device) {
+  std::lock_guard<std::mutex> lk(g_mutex);
+  return init_locked(device);
+}
+
+int pospopcnt_u8(const void* d_in, size_t n, uint64_t* d_counts, cudaStream_t stream) {
+  return count_impl(8, nullptr, true, d_in, n, d_counts, stream);
+}
+int pospopcnt_u16(const void* d_in, size_t n, uint64_t* d_counts, cudaStream_t stream) {
+  return count_impl(16, nullptr, true, d_in, n, d_counts, stream);
+}
+int pospopcnt_u32(const void* d_in, size_t n, uint64_t* d_counts, cudaStream_t stream) {
+  return count_impl(32, nullptr, true, d_in, n, d_counts, stream);
+}
+
+int pospopcnt_count(int width, int kernel, const void* d_in, size_t n, uint64_t* d_counts,
+                    cudaStream_t stream) {
+  if (kernel == POSPOPCNT_KERNEL_AUTO) return count_impl(width, nullptr, true, d_in, n, d_counts, stream);
+  if (kernel < 0 || kernel > POSPOPCNT_KERNEL_BALLOT) return POSPOPCNT_ERR_INVALID;
+  pospopcnt_config cfg = default_config();
+  cfg.kernel = kernel;
+  cfg.unroll = kernel == POSPOPCNT_KERNEL_BALLOT ? 2 : 4;
+  return count_impl(width, &cfg, true, d_in, n, d_counts, stream);
+}
+
+int pospopcnt_count_config(int width, const pospopcnt_config* cfg, const void* d_in, size_t n,
+                           uint64_t* d_counts, cudaStream_t stream) {
+  if (!cfg) return POSPOPCNT_ERR_INVALID;
+  return count_impl(width, cfg, true, d_in, n, d_counts, stream);
+}
+
+int pospopcnt_count_accumulate(int width, const void* d_in, size_t n, uint64_t* d_counts,
+                               cudaStream_t stream) {
+  return count_impl(width, nullptr, false, d_in, n, d_counts, stream);
+}
+
+int pospopcnt_count_host(int width, const void* h_in, size_t n, uint64_t* h_counts) {
+  int rc = POSPOPCNT_OK;
+  if (width_index(width) < 0 || !h_counts || (n > 0 && !h_in)) return POSPOPCNT_ERR_INVALID;
+  if (reinterpret_cast<uintptr_t>(h_in) % uintptr_t(width / 8) != 0) return POSPOPCNT_ERR_MISALIGNED;
+  DeviceState* st = current_state(&rc);
+  if (!st) return rc;
+  std::lock_guard<std::mutex> lk(g_host_mutex[st->device]);
+  cudaError_t e = cudaSuccess;
+  if (!st->d_acc) {
+    for (int i = 0; i < 2; ++i) {
+      if ((e = cudaMalloc(&st->d_stage[i], HOST_STAGE_BYTES)) != cudaSuccess) return cuda_fail(e);
+      if ((e = cudaStreamCreateWithFlags(&st->hstream[i], cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(e);
+      if ((e = cudaEventCreateWithFlags(&st->hevent[i], cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(e);
+    }
+    if ((e = cudaMalloc(reinterpret_cast<void**>(&st->d_acc), 64 * sizeof(uint64_t))) != cudaSuccess)
+      return cuda_fail(e);
+  }
+  cudaStream_t s0 = st->hstream[0], s1 = st->hstream[1];
+  const size_t wb = size_t(width / 8);
+  const size_t chunk_words = HOST_STAGE_BYTES / wb;
+  const pospopcnt_config cfg = config_for(*st, width, chunk_words);
+  if ((e = cudaMemsetAsync(st->d_acc, 0, sizeof(uint64_t) * size_t(width), s0)) != cudaSuccess)
+    return cuda_fail(e);
+  if ((e = cudaEventRecord(st->hevent[0], s0)) != cudaSuccess) return cuda_fail(e);
+  if ((e = cudaStreamWaitEvent(s1, st->hevent[0], 0)) != cudaSuccess) return cuda_fail(e);
+  const uint8_t* src = static_cast<const uint8_t*>(h_in);
+  size_t done = 0;
+  for (int j = 0; done < n; ++j) {
+    const size_t words = std::min(chunk_words, n - done);
+    cudaStream_t s = st->hstream[j & 1];
+    void* buf = st->d_stage[j & 1];
+    if ((e = cudaMemcpyAsync(buf, src + done * wb, words * wb, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+      return cuda_fail(e);
+    if ((rc = launch_plain(*st, width, cfg, buf, words, st->d_acc, s)) != POSPOPCNT_OK) return rc;
+    done += words;
+  }
+  if ((e = cudaEventRecord(st->hevent[1], s1)) != cudaSuccess) return cuda_fail(e);
+  if ((e = cudaStreamWaitEvent(s0, st->hevent[1], 0)) != cudaSuccess) return cuda_fail(e);
+  if ((e = cudaMemcpyAsync(h_counts, st->d_acc, sizeof(uint64_t) * size_t(width), cudaMemcpyDeviceToHost,
+                           s0)) != cudaSuccess)
+    return cuda_fail(e);
+  if ((e = cudaStreamSynchronize(s0)) != cudaSuccess) return cuda_fail(e);
+  return POSPOPCNT_OK;
+}
+
+int pospopcnt_batched(const void* d_in, const int64_t* d_offsets, size_t nseg, int width, uint64_t* d_counts,
+                      cudaStream_t stream) {
+  if (width_index(width) < 0) return POSPOPCNT_ERR_INVALID;
+  if (nseg == 0) return POSPOPCNT_OK;
+  if (!d_in || !d_offsets || !d_counts) return POSPOPCNT_ERR_INVALID;
+  if (reinterpret_cast<uintptr_t>(d_in) % uintptr_t(width / 8) != 0) return POSPOPCNT_ERR_MISALIGNED;
+  if (reinterpret_cast<uintptr_t>(d_offsets) % 8 != 0 || reinterpret_cast<uintptr_t>(d_counts) % 8 != 0)
+    return POSPOPCNT_ERR_MISALIGNED;
+  if (nseg > (size_t(1) << 40)) return POSPOPCNT_ERR_TOO_LARGE;
+  int rc = POSPOPCNT_OK;
+  DeviceState* st = current_state(&rc);
+  if (!st) return rc;
+  int slot;
+  {
+    std::lock_guard<std::mutex> lk(g_mutex);
+    auto& m = g_slots[st->device];
+    auto it = m.find(stream);
+    if (it != m.end()) {
+      slot = it->second;
+    } else {
+      if (int(m.size()) >= QUEUE_SLOTS) return POSPOPCNT_ERR_TOO_LARGE;
+      slot = int(m.size());
+      m.emplace(stream, slot);
+    }
+  }
+  cudaError_t e = cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * size_t(width) * nseg, stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  void* q = static_cast<char*>(st->d_queue) + size_t(slot) * QUEUE_SLOT_BYTES;
+  const int tile_words = (128 * 1024) / (width / 8);  // 128 KiB of input per tile
+  return launch_batched(*st, d_in, d_offsets, nseg, width, reinterpret_cast<unsigned long long*>(d_counts), q,
+                        tile_words, stream);
+}
+
+int pospopcnt_plain_segments(const void* d_in, const int64_t* h_offsets, size_t nseg, int width,
+                             uint64_t* d_counts, cudaStream_t stream) {
+  if (width_index(width) < 0) return POSPOPCNT_ERR_INVALID;
+  if (nseg == 0) return POSPOPCNT_OK;
+  if (!d_in || !h_offsets || !d_counts) return POSPOPCNT_ERR_INVALID;
+  for (size_t s = 0; s < nseg; ++s)
+    if (h_offsets[s] < 0 || h_offsets[s + 1] < h_offsets[s]) return POSPOPCNT_ERR_INVALID;
+  const size_t wb = size_t(width / 8);
+  const uint8_t* base = static_cast<const uint8_t*>(d_in);
+  for (size_t s = 0; s < nseg; ++s) {
+    const int rc = count_impl(width, nullptr, true, base + size_t(h_offsets[s]) * wb,
+                              size_t(h_offsets[s + 1] - h_offsets[s]), d_counts + s * size_t(width), stream);
+    if (rc != POSPOPCNT_OK) return rc;
+  }
+  return POSPOPCNT_OK;
+}
+
+int pospopcnt_check_device_error(cudaStream_t stream) {
+  int rc = POSPOPCNT_OK;
+  DeviceState* st = current_state(&rc);
+  if (!st) return rc;
+  cudaError_t e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  unsigned h = 0;
+  if ((e = cudaMemcpy(&h, st->d_err, sizeof h, cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(e);
+  if (h) {
+    if ((e = cudaMemset(st->d_err, 0, sizeof h)) != cudaSuccess) return cuda_fail(e);
+    return POSPOPCNT_ERR_TIMEOUT;
+  }
+  return POSPOPCNT_OK;
+}
+
+int pospopcnt_plan_split(int width, uint64_t addr, size_t n, size_t* head_words, size_t* body_vectors,
+                         size_t* tail_words) {
+  if (width_index(width) < 0 || !head_words || !body_vectors || !tail_words) return POSPOPCNT_ERR_INVALID;
+  if (addr % uint64_t(width / 8) != 0) return POSPOPCNT_ERR_MISALIGNED;
+  const Split s = plan_split(width, addr, n);
+  *head_words = s.head_words;
+  *body_vectors = s.body_vectors;
+  *tail_words = s.tail_words;
+  return POSPOPCNT_OK;
+}
+
+int pospopcnt_get_config(int width, size_t n, pospopcnt_config* cfg) {
+  if (width_index(width) < 0 || !cfg) return POSPOPCNT_ERR_INVALID;
+  int rc = POSPOPCNT_OK;
+  DeviceState* st = current_state(&rc);
+  if (!st) return rc;
+  *cfg = config_for(*st, width, n);
+  return normalize_config(*st, width, cfg);
+}
+
+int pospopcnt_set_config(int width, int size_class_, const pospopcnt_config* cfg) {
+  if (width_index(width) < 0 || !cfg || size_class_ < -1 || size_class_ >= NCLASSES) return POSPOPCNT_ERR_INVALID;
+  int rc = POSPOPCNT_OK;
+  DeviceState* st = current_state(&rc);
+  if (!st) return rc;
+  pospopcnt_config c = *cfg;
+  if ((rc = normalize_config(*st, width, &c)) != POSPOPCNT_OK) return rc;
+  std::lock_guard<std::mutex> lk(g_mutex);
+  for (int k = 0; k < NCLASSES; ++k)
+    if (size_class_ == -1 || k == size_class_) g_cfg[st->device][width_index(width)][k] = c;
+  return POSPOPCNT_OK;
+}
+
+int pospopcnt_autotune(int width, const void* d_in, size_t n, uint64_t* d_scratch_counts, pospopcnt_config* best,
+                       float* best_ms) {
+  int rc = check_args(width, d_in, n, d_scratch_counts);
+  if (rc != POSPOPCNT_OK) return rc;
+  if (!best || n == 0) return POSPOPCNT_ERR_INVALID;
+  DeviceState* st = current_state(&rc);
+  if (!st) return rc;
+  std::vector<pospopcnt_config> cands;
+  for (int t : {128, 256, 512})
+    for (int u : {2, 4, 8}) {
+      pospopcnt_config c = default_config();
+      c.kernel = POSPOPCNT_KERNEL_CSA, c.threads = t, c.unroll = u;
+      cands.push_back(c);
+    }
+  for (int s : {2, 3, 4, 6, 8})
+    for (int ch : {16384, 32768, 65536}) {
+      pospopcnt_config c = default_config();
+      c.kernel = POSPOPCNT_KERNEL_TMA, c.stages = s, c.chunk_bytes = ch;
+      if (normalize_config(*st, width, &c) == POSPOPCNT_OK) cands.push_back(c);
+    }
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e);
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  std::vector<uint64_t> ref(static_cast<size_t>(width), 0), got(static_cast<size_t>(width), 0);
+  float best_t = 1e30f;
+  int best_i = -1;
+  rc = POSPOPCNT_OK;
+  const int reps = 5;
+  for (size_t i = 0; i < cands.size() && rc == POSPOPCNT_OK; ++i) {
+    for (int w = 0; w < 2 && rc == POSPOPCNT_OK; ++w)
+      rc = count_impl(width, &cands[i], true, d_in, n, d_scratch_counts, s);
+    if (rc != POSPOPCNT_OK) break;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps && rc == POSPOPCNT_OK; ++r)
+      rc = count_impl(width, &cands[i], true, d_in, n, d_scratch_counts, s);
+    cudaEventRecord(e1, s);
+    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
+      rc = cuda_fail(e);
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= reps;
+    cudaMemcpy(got.data(), d_scratch_counts, sizeof(uint64_t) * size_t(width), cudaMemcpyDeviceToHost);
+    if (i == 0) {
+      ref = got;
+    } else if (got != ref) {
+      rc = POSPOPCNT_ERR_INVALID;  // candidates disagree: refuse to tune
+      break;
+    }
+    if (ms < best_t) best_t = ms, best_i = int(i);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  if (rc != POSPOPCNT_OK) return rc;
+  *best = cands[size_t(best_i)];
+  if (best_ms) *best_ms = best_t;
+  std::lock_guard<std::mutex> lk(g_mutex);
+  g_cfg[st->device][width_index(width)][size_class(uint64_t(n) * uint64_t(width / 8))] = *best;
+  return POSPOPCNT_OK;
+}
+
+const char* pospopcnt_strerror(int status) {
+  switch (status) {
+    case POSPOPCNT_OK: return "ok";
+    case POSPOPCNT_ERR_INVALID: return "invalid argument";
+    case POSPOPCNT_ERR_MISALIGNED: return "pointer not aligned to the word size";
+    case POSPOPCNT_ERR_CUDA: return "CUDA runtime error (see pospopcnt_last_cuda_error)";
+    case POSPOPCNT_ERR_NOT_INITIALIZED: return "no usable CUDA device";
+    case POSPOPCNT_ERR_TIMEOUT: return "a bounded device-side wait gave up";
+    case POSPOPCNT_ERR_TOO_LARGE: return "size beyond a documented limit";
+  }
+  return "unknown status";
+}
+
+int pospopcnt_last_cuda_error(void) { return t_last_cuda; }
+
+uint64_t pospopcnt_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

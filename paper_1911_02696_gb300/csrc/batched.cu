@@ -1,0 +1,187 @@
+// Segmented pospopcnt in one persistent launch.
+//
+// Segment s covers words [offsets[s], offsets[s+1]).  The word range
+// [offsets[0], offsets[nseg]) is cut into tiles of `tile_words` words whose
+// inner boundaries fall on 16-byte addresses.  Persistent CTAs pop tile
+// indices from an atomic work queue; a CTA splits its tile into one
+// contiguous sub-range per warp.  A warp finds the segment holding the first
+// word of its sub-range with a 32-way search over the offsets, then walks the
+// pieces (segment ∩ sub-range): each piece is counted like a plain call --
+// unaligned head and ragged tail word by word, the body in 16-byte vectors
+// through the carry-save circuit F_4 (§2, §4.1) with popc flushes -- and its
+// counts are reduced across the warp and added with one 64-bit atomic per
+// position into the segment's row.  Rows are zeroed beforehand by a memset.
+//
+// The queue counter lives in a 128-byte slot of the library's workspace; the
+// last CTA to finish resets it, so consecutive launches on one stream (and
+// replays of a captured graph) reuse the slot without a memset.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace ppc {
+
+struct QueueSlot {
+  unsigned long long next;  // next tile index to hand out
+  unsigned int done;        // CTAs that have finished
+};
+
+struct BatchedArgs {
+  const uint8_t* base;
+  const int64_t* offsets;
+  uint64_t nseg;
+  unsigned long long* counts;
+  QueueSlot* q;
+  uint64_t tile_words;  // multiple of 8 warps x 16 bytes
+};
+
+constexpr int BT_THREADS = 256;
+constexpr int BT_WARPS = BT_THREADS / 32;
+
+// Largest s in [0, nseg) with offsets[s] <= w (requires offsets[0] <= w <
+// offsets[nseg]).  Each round the 32 lanes probe 32 evenly spaced candidates.
+__device__ __forceinline__ uint64_t find_segment(const int64_t* offsets, uint64_t nseg, int64_t w) {
+  const int lane = threadIdx.x & 31;
+  uint64_t lo = 0, hi = nseg - 1;  // answer in [lo, hi]
+  while (hi > lo) {
+    const uint64_t span = hi - lo + 1;
+    const uint64_t step = (span + 31) / 32;
+    const uint64_t idx = lo + uint64_t(lane) * step;
+    const bool le = idx <= hi && offsets[idx] <= w;
+    const unsigned m = __ballot_sync(FULL_MASK, le);  // lane 0 always true
+    const int j = 31 - __clz(m);
+    lo = lo + uint64_t(j) * step;
+    const uint64_t nhi = lo + step - 1;
+    hi = nhi < hi ? nhi : hi;
+    if (step == 1) break;
+  }
+  return lo;
+}
+
+// Counts words [pa, pb) of `base` with the whole warp and adds the result to
+// row[0..K-1].
+template <int K>
+__device__ __forceinline__ void warp_count_piece(const uint8_t* base, uint64_t pa, uint64_t pb,
+                                                 unsigned long long* row) {
+  constexpr int WB = K / 8;
+  constexpr int SH = 5 - ilog2<K>::value;
+  const int lane = threadIdx.x & 31;
+  const uint64_t A = reinterpret_cast<uint64_t>(base) + pa * WB;
+  const uint64_t E = reinterpret_cast<uint64_t>(base) + pb * WB;
+  uint64_t bodyA = (A + 15) & ~uint64_t(15);
+  if (bodyA > E) bodyA = E;
+  uint64_t bodyE = E & ~uint64_t(15);
+  if (bodyE < bodyA) bodyE = bodyA;
+  const uint64_t nvec = (bodyE - bodyA) / 16;
+  const uint32_t head_words = uint32_t((bodyA - A) / WB);
+  const uint32_t tail_words = uint32_t((E - bodyE) / WB);
+
+  uint32_t B[4] = {0, 0, 0, 0};
+  uint32_t top[K];
+#pragma unroll
+  for (int p = 0; p < K; ++p) top[p] = 0;
+  const uint4* vp = reinterpret_cast<const uint4*>(bodyA);
+  for (uint64_t bv = 0; bv < nvec; bv += 128) {  // 32 lanes x 4 vectors per trip
+    uint32_t d[16];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint64_t idx = bv + uint64_t(j) * 32 + lane;
+      const uint4 x = idx < nvec ? ld_stream(vp + idx) : make_uint4(0, 0, 0, 0);
+      d[4 * j + 0] = x.x, d[4 * j + 1] = x.y, d[4 * j + 2] = x.z, d[4 * j + 3] = x.w;
+    }
+    flush<K>(top, Circuit<4>::run(d, B));
+  }
+  uint32_t c[K];
+  finalize<K, 4>(c, top, B);
+  if (uint32_t(lane) < head_words)
+    count_word<K>(c, load_word<K>(reinterpret_cast<const uint8_t*>(A) + lane * WB));
+  if (lane >= 16 && uint32_t(lane - 16) < tail_words)
+    count_word<K>(c, load_word<K>(reinterpret_cast<const uint8_t*>(bodyE) + (lane - 16) * WB));
+  const uint32_t v = warp_reduce_positions<K>(c);
+  if ((lane & ((1 << SH) - 1)) == 0 && v) atomicAdd(row + (lane >> SH), (unsigned long long)v);
+}
+
+template <int K>
+__global__ void __launch_bounds__(BT_THREADS) batched_kernel(BatchedArgs a) {
+  constexpr int WB = K / 8;
+  __shared__ unsigned long long s_tile;
+  const int warp = threadIdx.x >> 5;
+  const int64_t o0 = a.offsets[0];
+  const int64_t oN = a.offsets[a.nseg];
+  // first tile starts at the 16-byte boundary at or before word o0
+  const uint64_t mis = (reinterpret_cast<uint64_t>(a.base) + uint64_t(o0) * WB) & 15;
+  const int64_t start = o0 - int64_t(mis / WB);
+  const uint64_t T = a.tile_words, Tw = a.tile_words / BT_WARPS;
+
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(&a.q->next, 1ull);
+    __syncthreads();
+    const uint64_t tile = s_tile;
+    __syncthreads();
+    if (oN <= start || tile >= (uint64_t(oN - start) + T - 1) / T) break;
+    const int64_t t0 = start + int64_t(tile * T);
+    int64_t w0 = t0 + int64_t(warp * Tw);
+    int64_t w1 = w0 + int64_t(Tw);
+    if (w0 < o0) w0 = o0;
+    if (w1 > oN) w1 = oN;
+    if (w0 >= w1) continue;
+    uint64_t s = find_segment(a.offsets, a.nseg, w0);
+    int64_t seg_lo = a.offsets[s];
+    for (;;) {
+      const int64_t seg_hi = a.offsets[s + 1];
+      const int64_t pa = seg_lo > w0 ? seg_lo : w0;
+      const int64_t pb = seg_hi < w1 ? seg_hi : w1;
+      if (pa < pb) warp_count_piece<K>(a.base, uint64_t(pa), uint64_t(pb), a.counts + s * K);
+      if (seg_hi >= w1 || s + 1 >= a.nseg) break;
+      ++s;
+      seg_lo = seg_hi;
+    }
+  }
+  // the last CTA out resets the queue slot for the next launch
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(&a.q->done, 1u);
+    if (prev == gridDim.x - 1) {
+      atomicExch(&a.q->next, 0ull);
+      atomicExch(&a.q->done, 0u);
+      __threadfence();
+    }
+  }
+}
+
+template <int K>
+static int launch_batched_k(const DeviceState& st, const BatchedArgs& a, cudaStream_t stream) {
+  auto kern = batched_kernel<K>;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, BT_THREADS, 0) != cudaSuccess || occ < 1)
+    occ = 1;
+  const unsigned grid = unsigned(st.sms) * unsigned(occ);
+  kern<<<grid, BT_THREADS, 0, stream>>>(a);
+  note_launch();
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? POSPOPCNT_OK : cuda_fail(e);
+}
+
+int launch_batched(const DeviceState& st, const void* d_in, const int64_t* d_offsets, size_t nseg,
+                   int width, unsigned long long* d_counts, void* queue_slot, int tile_words,
+                   cudaStream_t stream) {
+  BatchedArgs a;
+  a.base = static_cast<const uint8_t*>(d_in);
+  a.offsets = d_offsets;
+  a.nseg = nseg;
+  a.counts = d_counts;
+  a.q = static_cast<QueueSlot*>(queue_slot);
+  a.tile_words = uint64_t(tile_words);
+  switch (width) {
+    case 8: return launch_batched_k<8>(st, a, stream);
+    case 16: return launch_batched_k<16>(st, a, stream);
+    case 32: return launch_batched_k<32>(st, a, stream);
+  }
+  return POSPOPCNT_ERR_INVALID;
+}
+
+}  // namespace ppc

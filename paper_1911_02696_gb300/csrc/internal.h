@@ -1,0 +1,61 @@
+// Internal interfaces between the translation units of the library.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime_api.h>
+
+#include "pospopcnt.h"
+
+namespace ppc {
+
+// Per-device state owned by the library (created by pospopcnt_init).
+struct DeviceState {
+  bool ready = false;
+  int device = -1;
+  int sms = 0;
+  int smem_optin = 0;
+  unsigned* d_err = nullptr;      // device error word
+  void* d_queue = nullptr;        // batched work-queue slots (QUEUE_SLOTS x 128 B)
+  // host-buffer path
+  void* d_stage[2] = {nullptr, nullptr};
+  unsigned long long* d_acc = nullptr;
+  cudaStream_t hstream[2] = {nullptr, nullptr};
+  cudaEvent_t hevent[2] = {nullptr, nullptr};
+};
+
+constexpr int QUEUE_SLOTS = 256;
+constexpr int QUEUE_SLOT_BYTES = 128;
+constexpr size_t HOST_STAGE_BYTES = size_t(64) << 20;
+
+// Returns the state of the current device, initialising it if needed, or
+// nullptr (with *status set) on failure.
+DeviceState* current_state(int* status);
+
+// Records a CUDA failure for pospopcnt_last_cuda_error and returns
+// POSPOPCNT_ERR_CUDA.
+int cuda_fail(cudaError_t e);
+
+// Counts one kernel launch.
+void note_launch();
+
+// Head / body / tail split of n words of `width` bits at addr.
+struct Split {
+  size_t head_words, body_vectors, tail_words;
+};
+Split plan_split(int width, uint64_t addr, size_t n);
+
+// Launch of one single-stream count (no memset; adds into d_counts).
+int launch_plain(const DeviceState& st, int width, const pospopcnt_config& cfg, const void* d_in,
+                 size_t n, unsigned long long* d_counts, cudaStream_t stream);
+
+// Validates a configuration for a width; fills defaults for zero fields.
+int normalize_config(const DeviceState& st, int width, pospopcnt_config* cfg);
+
+// Launch of the batched kernel (counts zeroed by the caller).
+int launch_batched(const DeviceState& st, const void* d_in, const int64_t* d_offsets, size_t nseg,
+                   int width, unsigned long long* d_counts, void* queue_slot, int tile_words,
+                   cudaStream_t stream);
+
+}  // namespace ppc

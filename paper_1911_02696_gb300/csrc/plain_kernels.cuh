@@ -1,0 +1,362 @@
+// Single-stream pospopcnt kernels and their host launcher, templated on the
+// word width K (8, 16, 32).  Each width is instantiated in its own
+// translation unit (plain_w8.cu, plain_w16.cu, plain_w32.cu).
+//
+//   csa_kernel    128-bit coalesced loads straight into registers, grid-stride,
+//                 `U` vectors per thread per trip = one circuit F_L over
+//                 4U registers (L = log2 4U), popc flush per trip.
+//   tma_kernel    persistent CTAs; one producer lane streams fixed-size chunks
+//                 with cp.async.bulk into an S-stage shared-memory ring guarded
+//                 by full/empty mbarriers; 8 consumer warps run F_4 over the
+//                 chunk from shared memory.  Every wait is bounded.
+//   ballot_kernel bit transpose by __ballot_sync: for each of the 32 bits of a
+//                 lane register, the warp's vote mask is popc'ed into the
+//                 counter of that bit's position (comparison kernel).
+//
+// All three count the unaligned head and the ragged tail word by word in
+// block 0 and finish with one 64-bit atomic add per position per block.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace ppc {
+
+struct PlainArgs {
+  const uint4* body;      // 16-byte aligned vectors
+  uint64_t nvec;          // number of vectors
+  const uint8_t* head;    // first head word
+  uint32_t head_words;
+  const uint8_t* tail;    // first tail word
+  uint32_t tail_words;
+  unsigned long long* counts;
+  unsigned* err;
+};
+
+template <int K, int NTHREADS>
+__device__ __forceinline__ void count_head_tail(uint32_t (&c)[K], const PlainArgs& a) {
+  static_assert(NTHREADS >= 64, "head/tail lanes need two warps");
+  if (blockIdx.x != 0) return;
+  const unsigned t = threadIdx.x;
+  if (t < a.head_words) count_word<K>(c, load_word<K>(a.head + t * (K / 8)));
+  if (t >= 32 && t - 32 < a.tail_words) count_word<K>(c, load_word<K>(a.tail + (t - 32) * (K / 8)));
+}
+
+// ---------------------------------------------------------------------------
+template <int K, int U, int NTHREADS>
+__global__ void __launch_bounds__(NTHREADS) csa_kernel(PlainArgs a) {
+  constexpr int R = 4 * U;
+  constexpr int L = ilog2<R>::value;
+  uint32_t B[L];
+#pragma unroll
+  for (int l = 0; l < L; ++l) B[l] = 0;
+  uint32_t top[K];
+#pragma unroll
+  for (int p = 0; p < K; ++p) top[p] = 0;
+
+  const uint64_t stride = uint64_t(gridDim.x) * NTHREADS;
+  uint64_t v = uint64_t(blockIdx.x) * NTHREADS + threadIdx.x;
+  const uint64_t reach = uint64_t(U - 1) * stride;
+  const uint64_t full_end = a.nvec > reach ? a.nvec - reach : 0;
+  for (; v < full_end; v += U * stride) {
+    uint32_t d[R];
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+      const uint4 x = ld_stream(a.body + v + i * stride);
+      d[4 * i + 0] = x.x, d[4 * i + 1] = x.y, d[4 * i + 2] = x.z, d[4 * i + 3] = x.w;
+    }
+    flush<K>(top, Circuit<L>::run(d, B));
+  }
+  if (v < a.nvec) {  // last, partial trip: missing vectors read as zero
+    uint32_t d[R];
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+      const uint64_t idx = v + i * stride;
+      const uint4 x = idx < a.nvec ? ld_stream(a.body + idx) : make_uint4(0, 0, 0, 0);
+      d[4 * i + 0] = x.x, d[4 * i + 1] = x.y, d[4 * i + 2] = x.z, d[4 * i + 3] = x.w;
+    }
+    flush<K>(top, Circuit<L>::run(d, B));
+  }
+  uint32_t c[K];
+  finalize<K, L>(c, top, B);
+  count_head_tail<K, NTHREADS>(c, a);
+  block_reduce_add<K, NTHREADS / 32>(c, a.counts);
+}
+
+// ---------------------------------------------------------------------------
+constexpr int TMA_CWARPS = 8;                       // consumer warps
+constexpr int TMA_THREADS = (TMA_CWARPS + 1) * 32;  // + one producer warp
+constexpr int TMA_MAX_STAGES = 16;
+constexpr int TMA_CHUNK_QUANTUM = 4 * TMA_CWARPS * 32 * 16;  // one F_4 per consumer thread
+
+struct TmaArgs {
+  PlainArgs p;
+  const uint8_t* body_bytes_ptr;
+  uint64_t body_bytes;  // multiple of 16
+  uint32_t chunk_bytes;  // multiple of TMA_CHUNK_QUANTUM
+  uint32_t stages;
+};
+
+template <int K>
+__global__ void __launch_bounds__(TMA_THREADS) tma_kernel(TmaArgs a) {
+  extern __shared__ __align__(128) uint8_t ring[];
+  __shared__ __align__(8) uint64_t full[TMA_MAX_STAGES];
+  __shared__ __align__(8) uint64_t empty[TMA_MAX_STAGES];
+  __shared__ uint32_t s_issued;              // chunks the producer issued
+  __shared__ uint32_t s_consumed[TMA_CWARPS];  // chunks each consumer warp finished
+  __shared__ uint32_t s_abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t S = a.stages;
+  const uint64_t nchunks = (a.body_bytes + a.chunk_bytes - 1) / a.chunk_bytes;
+  const uint32_t my_chunks =
+      blockIdx.x < nchunks ? uint32_t((nchunks - 1 - blockIdx.x) / gridDim.x + 1) : 0u;
+
+  if (threadIdx.x == 0) {
+    for (uint32_t s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], TMA_CWARPS);
+    }
+    s_issued = 0;
+    s_abort = 0;
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  uint32_t c[K];
+#pragma unroll
+  for (int p = 0; p < K; ++p) c[p] = 0;
+
+  if (warp == TMA_CWARPS) {
+    // producer: one lane issues every copy
+    if (lane == 0) {
+      uint32_t i = 0;
+      for (; i < my_chunks; ++i) {
+        const uint32_t s = i % S, use = i / S;
+        if (use > 0 && !mbar_wait_bounded(&empty[s], (use - 1) & 1u, WAIT_LIMIT_NS)) {
+          atomicOr(a.p.err, ERR_BIT_TIMEOUT_EMPTY);
+          atomicExch(&s_abort, 1u);
+          break;
+        }
+        if (*((volatile uint32_t*)&s_abort)) break;
+        const uint64_t chunk = blockIdx.x + uint64_t(i) * gridDim.x;
+        const uint64_t off = chunk * a.chunk_bytes;
+        const uint64_t rem = a.body_bytes - off;
+        const uint32_t bytes = rem < a.chunk_bytes ? uint32_t(rem) : a.chunk_bytes;
+        mbar_arrive_expect_tx(&full[s], bytes);
+        bulk_g2s(ring + size_t(s) * a.chunk_bytes, a.body_bytes_ptr + off, bytes, &full[s]);
+      }
+      s_issued = i;
+    }
+  } else {
+    // consumers
+    constexpr int CT = TMA_CWARPS * 32;
+    uint32_t B[4] = {0, 0, 0, 0};
+    uint32_t top[K];
+#pragma unroll
+    for (int p = 0; p < K; ++p) top[p] = 0;
+    uint32_t i = 0;
+    for (; i < my_chunks; ++i) {
+      const uint32_t s = i % S, use = i / S;
+      // every lane waits (each acquires the copied bytes); the verdict is
+      // made warp-uniform so the warp leaves the loop together
+      const bool ok = __all_sync(FULL_MASK, mbar_wait_bounded(&full[s], use & 1u, WAIT_LIMIT_NS));
+      if (!ok) {
+        if (lane == 0) {
+          atomicOr(a.p.err, ERR_BIT_TIMEOUT_FULL);
+          atomicExch(&s_abort, 1u);
+        }
+        break;
+      }
+      const uint64_t chunk = blockIdx.x + uint64_t(i) * gridDim.x;
+      const uint64_t off = chunk * a.chunk_bytes;
+      const uint64_t rem = a.body_bytes - off;
+      const uint32_t nv = (rem < a.chunk_bytes ? uint32_t(rem) : a.chunk_bytes) / 16u;
+      const uint4* sv = reinterpret_cast<const uint4*>(ring + size_t(s) * a.chunk_bytes);
+      for (uint32_t base = 0; base < nv; base += 4 * CT) {
+        uint32_t d[16];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const uint32_t idx = base + j * CT + threadIdx.x;
+          const uint4 x = idx < nv ? sv[idx] : make_uint4(0, 0, 0, 0);
+          d[4 * j + 0] = x.x, d[4 * j + 1] = x.y, d[4 * j + 2] = x.z, d[4 * j + 3] = x.w;
+        }
+        flush<K>(top, Circuit<4>::run(d, B));
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
+      if (__any_sync(FULL_MASK, *((volatile uint32_t*)&s_abort) != 0u)) {
+        ++i;
+        break;
+      }
+    }
+    if (lane == 0) s_consumed[warp] = i;
+    finalize<K, 4>(c, top, B);
+  }
+  __syncthreads();
+  // After an abort, wait (bounded) for copies still in flight before the
+  // shared memory they target goes away.
+  if (s_abort && threadIdx.x == 0) {
+    uint32_t lo = s_issued;
+    for (int w = 0; w < TMA_CWARPS; ++w) lo = s_consumed[w] < lo ? s_consumed[w] : lo;
+    for (uint32_t i = lo; i < s_issued; ++i) {
+      if (!mbar_wait_bounded(&full[i % S], (i / S) & 1u, WAIT_LIMIT_NS)) {
+        atomicOr(a.p.err, ERR_BIT_TIMEOUT_DRAIN);
+        break;
+      }
+    }
+  }
+  count_head_tail<K, TMA_THREADS>(c, a.p);
+  block_reduce_add<K, TMA_CWARPS + 1>(c, a.p.counts);
+}
+
+// ---------------------------------------------------------------------------
+template <int K, int U, int NTHREADS>
+__global__ void __launch_bounds__(NTHREADS) ballot_kernel(PlainArgs a) {
+  uint32_t acc[K];
+#pragma unroll
+  for (int p = 0; p < K; ++p) acc[p] = 0;
+  const int lane = threadIdx.x & 31;
+  const uint64_t gw = (uint64_t(blockIdx.x) * NTHREADS + threadIdx.x) >> 5;
+  const uint64_t nw = uint64_t(gridDim.x) * (NTHREADS / 32);
+  for (uint64_t base = gw * 32 * U; base < a.nvec; base += nw * 32 * U) {  // warp-uniform
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+      const uint64_t idx = base + uint64_t(i) * 32 + lane;
+      const uint4 x = idx < a.nvec ? ld_stream(a.body + idx) : make_uint4(0, 0, 0, 0);
+      const uint32_t r[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+#pragma unroll
+        for (int b = 0; b < 32; ++b) acc[b & (K - 1)] += __popc(__ballot_sync(FULL_MASK, (r[q] >> b) & 1u));
+      }
+    }
+  }
+  uint32_t c[K];
+#pragma unroll
+  for (int p = 0; p < K; ++p) c[p] = lane == 0 ? acc[p] : 0u;  // every lane holds the warp total
+  count_head_tail<K, NTHREADS>(c, a);
+  block_reduce_add<K, NTHREADS / 32>(c, a.counts);
+}
+
+// ---------------------------------------------------------------------------
+// Host launcher for width K.
+
+template <typename Kern>
+static int occupancy(Kern kern, int threads, size_t smem) {
+  int blocks = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, threads, smem) != cudaSuccess)
+    return 1;
+  return blocks > 0 ? blocks : 1;
+}
+
+// Per-block u32 partial sums stay exact while one block sees fewer than
+// 2^31 bytes.
+static inline uint64_t min_blocks_for(uint64_t nbytes) { return (nbytes >> 31) + 1; }
+
+template <int K, int U, int T>
+static int launch_csa(const DeviceState& st, const PlainArgs& a, int bps, cudaStream_t stream) {
+  auto kern = csa_kernel<K, U, T>;
+  const int occ = occupancy(kern, T, 0);
+  const uint64_t cap = uint64_t(st.sms) * uint64_t(std::min(bps > 0 ? bps : occ, occ));
+  const uint64_t need = (a.nvec + uint64_t(U) * T - 1) / (uint64_t(U) * T);
+  uint64_t grid = std::max<uint64_t>(1, std::min(cap, need));
+  grid = std::max(grid, min_blocks_for(a.nvec * 16));
+  kern<<<unsigned(grid), T, 0, stream>>>(a);
+  note_launch();
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? POSPOPCNT_OK : cuda_fail(e);
+}
+
+template <int K, int U, int T>
+static int launch_ballot(const DeviceState& st, const PlainArgs& a, int bps, cudaStream_t stream) {
+  auto kern = ballot_kernel<K, U, T>;
+  const int occ = occupancy(kern, T, 0);
+  const uint64_t cap = uint64_t(st.sms) * uint64_t(std::min(bps > 0 ? bps : occ, occ));
+  const uint64_t per = uint64_t(32) * U * (T / 32);
+  const uint64_t need = (a.nvec + per - 1) / per;
+  uint64_t grid = std::max<uint64_t>(1, std::min(cap, need));
+  grid = std::max(grid, min_blocks_for(a.nvec * 16));
+  kern<<<unsigned(grid), T, 0, stream>>>(a);
+  note_launch();
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? POSPOPCNT_OK : cuda_fail(e);
+}
+
+template <int K>
+static int launch_tma(const DeviceState& st, const PlainArgs& p, int bps, int stages, int chunk,
+                      cudaStream_t stream) {
+  auto kern = tma_kernel<K>;
+  const size_t smem = size_t(stages) * size_t(chunk);
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
+    return cuda_fail(cudaGetLastError());
+  TmaArgs a;
+  a.p = p;
+  a.body_bytes_ptr = reinterpret_cast<const uint8_t*>(p.body);
+  a.body_bytes = p.nvec * 16;
+  a.chunk_bytes = uint32_t(chunk);
+  a.stages = uint32_t(stages);
+  const int occ = occupancy(kern, TMA_THREADS, smem);
+  const uint64_t cap = uint64_t(st.sms) * uint64_t(std::min(bps > 0 ? bps : occ, occ));
+  const uint64_t nchunks = (a.body_bytes + chunk - 1) / chunk;
+  uint64_t grid = std::max<uint64_t>(1, std::min(cap, nchunks));
+  grid = std::max(grid, std::min<uint64_t>(nchunks, min_blocks_for(a.body_bytes)));
+  kern<<<unsigned(grid), TMA_THREADS, smem, stream>>>(a);
+  note_launch();
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? POSPOPCNT_OK : cuda_fail(e);
+}
+
+template <int K, int T>
+static int launch_csa_u(const DeviceState& st, const PlainArgs& a, const pospopcnt_config& cfg,
+                        cudaStream_t stream) {
+  switch (cfg.unroll) {
+    case 2: return launch_csa<K, 2, T>(st, a, cfg.blocks_per_sm, stream);
+    case 4: return launch_csa<K, 4, T>(st, a, cfg.blocks_per_sm, stream);
+    case 8: return launch_csa<K, 8, T>(st, a, cfg.blocks_per_sm, stream);
+  }
+  return POSPOPCNT_ERR_INVALID;
+}
+
+template <int K>
+int launch_plain_k(const DeviceState& st, const pospopcnt_config& cfg, const void* d_in, size_t n,
+                   unsigned long long* d_counts, cudaStream_t stream) {
+  const Split sp = plan_split(K, reinterpret_cast<uint64_t>(d_in), n);
+  const uint8_t* base = static_cast<const uint8_t*>(d_in);
+  PlainArgs a;
+  a.head = base;
+  a.head_words = uint32_t(sp.head_words);
+  a.body = reinterpret_cast<const uint4*>(base + sp.head_words * (K / 8));
+  a.nvec = sp.body_vectors;
+  a.tail = base + sp.head_words * (K / 8) + sp.body_vectors * 16;
+  a.tail_words = uint32_t(sp.tail_words);
+  a.counts = d_counts;
+  a.err = st.d_err;
+  if (a.nvec == 0 && a.head_words == 0 && a.tail_words == 0) return POSPOPCNT_OK;
+  switch (cfg.kernel) {
+    case POSPOPCNT_KERNEL_CSA:
+      switch (cfg.threads) {
+        case 128: return launch_csa_u<K, 128>(st, a, cfg, stream);
+        case 256: return launch_csa_u<K, 256>(st, a, cfg, stream);
+        case 512: return launch_csa_u<K, 512>(st, a, cfg, stream);
+      }
+      return POSPOPCNT_ERR_INVALID;
+    case POSPOPCNT_KERNEL_TMA:
+      if (a.nvec == 0) return launch_csa<K, 4, 256>(st, a, 1, stream);  // head/tail only
+      return launch_tma<K>(st, a, cfg.blocks_per_sm, cfg.stages, cfg.chunk_bytes, stream);
+    case POSPOPCNT_KERNEL_BALLOT:
+      switch (cfg.unroll) {
+        case 1: return launch_ballot<K, 1, 256>(st, a, cfg.blocks_per_sm, stream);
+        case 2: return launch_ballot<K, 2, 256>(st, a, cfg.blocks_per_sm, stream);
+        case 4: return launch_ballot<K, 4, 256>(st, a, cfg.blocks_per_sm, stream);
+      }
+      return POSPOPCNT_ERR_INVALID;
+  }
+  return POSPOPCNT_ERR_INVALID;
+}
+
+}  // namespace ppc

@@ -1,0 +1,249 @@
+"""Parity of the single-stream CUDA path with the CPU oracle: bit-exact
+(tolerance 0) for every kernel family and width, for every start alignment,
+for every small length, across tiles and ragged tails, at the full 2 GiB
+workloads, and on the edge cases (empty, all-ones, all-zeros, one-hot,
+sparse).  Guard bytes of 0xFF surround every input slice, so a kernel that
+read and counted a byte outside its input would fail parity; guard words
+after the counts catch stray writes."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+import paper_1911_02696_gb300 as ppc  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+WIDTHS = (8, 16, 32)
+KERNELS = ("csa", "tma", "ballot")
+DT = {8: np.uint8, 16: np.uint16, 32: np.uint32}
+GUARD = 256
+SENTINEL = -7
+
+
+def _device_slice(words: np.ndarray, offset: int):
+    """A device copy of `words` starting `offset` bytes past a 256-byte
+    boundary, with 0xFF guard bytes on both sides."""
+    b = np.ascontiguousarray(words).view(np.uint8)
+    buf = torch.full((GUARD + offset + b.size + GUARD,), 0xFF, dtype=torch.uint8, device="cuda")
+    if b.size:
+        buf[GUARD + offset: GUARD + offset + b.size].copy_(torch.from_numpy(b))
+    return buf, buf[GUARD + offset: GUARD + offset + b.size]
+
+
+def _counts_with_guard(width):
+    c = torch.full((width + 8,), SENTINEL, dtype=torch.int64, device="cuda")
+    return c, c[:width]
+
+
+def _as_u64(t):
+    return t.cpu().numpy().view(np.uint64)
+
+
+def run_kernel(width, kernel, x, out, cfg=None):
+    if cfg is not None:
+        return ppc.pospopcnt_count_config(width, cfg, x, counts=out)
+    if kernel is None:
+        return {8: ppc.pospopcnt_u8, 16: ppc.pospopcnt_u16, 32: ppc.pospopcnt_u32}[width](x, counts=out)
+    return ppc.pospopcnt_count(width, x, kernel, counts=out)
+
+
+def check(width, kernel, words, offset=0, cfg=None):
+    _, x = _device_slice(words, offset)
+    full, out = _counts_with_guard(width)
+    run_kernel(width, kernel, x, out, cfg)
+    torch.cuda.synchronize()
+    got = _as_u64(out)
+    ref = oracle.pospopcnt(words, width)
+    assert np.array_equal(got, ref), (width, kernel, words.size, offset, got, ref)
+    assert torch.all(full[width:] == SENTINEL)
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_every_small_length_and_alignment(width, kernel):
+    """n = 0..299 words at every word-aligned start offset 0..15 bytes."""
+    wb = width // 8
+    words = synth.uniform_bits(1000 + width, 300, width)
+    for offset in range(0, 16, wb):
+        _, x_all = _device_slice(words, offset)
+        full = torch.full((300, width + 8), SENTINEL, dtype=torch.int64, device="cuda")
+        for n in range(300):
+            run_kernel(width, kernel, x_all[: n * wb], full[n, :width])
+        torch.cuda.synchronize()
+        got = full.cpu().numpy()
+        for n in range(300):
+            ref = oracle.pospopcnt(words[:n], width)
+            assert np.array_equal(got[n, :width].view(np.uint64), ref), (offset, n)
+            assert np.all(got[n, width:] == SENTINEL)
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_ragged_multi_tile(width, kernel):
+    """Sizes that span many CTAs and leave partial trips, ragged tails and
+    partial TMA chunks."""
+    rng = np.random.default_rng(width * 7 + len(kernel))
+    for i in range(6):
+        nbytes = int(rng.integers(1 << 16, 48 << 20))
+        n = nbytes // (width // 8)
+        offset = int(rng.integers(0, 16 // (width // 8))) * (width // 8)
+        check(width, kernel, synth.uniform_bits(2000 + i, n, width), offset)
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_special_inputs(width):
+    n = (1 << 22) + 5
+    dt = DT[width]
+    for kernel in KERNELS:
+        check(width, kernel, np.full(n, (1 << width) - 1, dtype=dt), 0)
+        check(width, kernel, np.zeros(n, dtype=dt), width // 8)
+        check(width, kernel, synth.one_hot(3, n, width), 0)
+        check(width, kernel, synth.sparse(4, n, width), 0)
+        check(width, kernel, np.zeros(0, dtype=dt), 0)
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_every_config(width):
+    """Every configuration the autotuner may pick gives the same counts."""
+    words = synth.uniform_bits(77, (9 << 20) // (width // 8) + 3, width)
+    cfgs = [dict(kernel="csa", threads=t, unroll=u) for t in (128, 256, 512) for u in (2, 4, 8)]
+    cfgs += [dict(kernel="tma", stages=s, chunk_bytes=c) for s in (2, 3, 4, 6, 8)
+             for c in (16384, 32768, 65536) if s * c <= 196608]
+    cfgs += [dict(kernel="ballot", unroll=u) for u in (1, 2, 4)]
+    cfgs += [dict(kernel="csa", blocks_per_sm=1), dict(kernel="tma", blocks_per_sm=1, stages=2)]
+    for cfg in cfgs:
+        check(width, None, words, 2 * (width // 8) % 16, cfg)
+
+
+def test_accumulate_form():
+    words = synth.uniform_bits(5, 1 << 20, 16)
+    _, x = _device_slice(words, 0)
+    c = torch.zeros(16, dtype=torch.int64, device="cuda")
+    ppc.pospopcnt_count_accumulate(16, x, c)
+    ppc.pospopcnt_count_accumulate(16, x[: (1 << 19) * 2], c)
+    torch.cuda.synchronize()
+    ref = oracle.pospopcnt(words) + oracle.pospopcnt(words[: 1 << 19])
+    assert np.array_equal(_as_u64(c), ref)
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_host_buffer_path(width):
+    """pospopcnt_count_host: chunked copies through the staging buffers."""
+    for nbytes in (0, 2, 4096 + 4, (64 << 20) - 4, (64 << 20) + 12, (200 << 20) + 4):
+        n = nbytes // (width // 8)
+        words = synth.uniform_bits(600 + nbytes % 97, n, width)
+        got = ppc.pospopcnt_count_host(width, words)
+        assert np.array_equal(got, oracle.pospopcnt(words, width)), nbytes
+    pinned = torch.from_numpy(synth.uniform_bits(9, 3 << 20, width).view(np.uint8)).pin_memory()
+    got = ppc.pospopcnt_count_host(width, pinned)
+    assert np.array_equal(got, oracle.pospopcnt(pinned.numpy(), width))
+
+
+def test_autotune_installs_a_valid_config():
+    words = synth.uniform_bits(8, 32 << 20, 16)
+    _, x = _device_slice(words, 0)
+    best, ms = ppc.pospopcnt_autotune(16, x)
+    assert ms > 0 and best["kernel"] in (1, 2)
+    assert ppc.pospopcnt_get_config(16, words.size)["kernel"] == best["kernel"]
+    check(16, None, words)
+
+
+def test_bounded_wait_reports_timeout():
+    """A wait that can never be satisfied gives up and the host reads
+    ERR_TIMEOUT; the context stays usable afterwards."""
+    assert ppc.pospopcnt_check_device_error() == 0
+    ppc.pospopcnt_selftest_timeout(2_000_000)  # 2 ms
+    assert ppc.pospopcnt_check_device_error() == 5
+    assert ppc.pospopcnt_check_device_error() == 0
+    check(16, "tma", synth.uniform_bits(1, 1 << 16, 16))
+
+
+def test_launch_counter_counts_kernels():
+    x = torch.zeros(1 << 20, dtype=torch.uint8, device="cuda")
+    before = ppc.pospopcnt_launch_count()
+    for _ in range(5):
+        ppc.pospopcnt_u16(x)
+    assert ppc.pospopcnt_launch_count() - before == 5
+
+
+def test_stream_ordering_on_side_stream():
+    words = synth.uniform_bits(10, 1 << 22, 32)
+    _, x = _device_slice(words, 0)
+    s = torch.cuda.Stream()
+    out = torch.empty(32, dtype=torch.int64, device="cuda")
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        ppc.pospopcnt_u32(x, counts=out, stream=s)
+    s.synchronize()
+    assert np.array_equal(_as_u64(out), oracle.pospopcnt(words, 32))
+
+
+def test_graph_capture_of_plain_call():
+    words = synth.uniform_bits(11, 1 << 21, 16)
+    _, x = _device_slice(words, 2)
+    out = torch.empty(16, dtype=torch.int64, device="cuda")
+    ppc.pospopcnt_init(torch.cuda.current_device())
+    ppc.pospopcnt_u16(x, counts=out)  # warm-up outside capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        ppc.pospopcnt_u16(x, counts=out)
+    out.fill_(0)
+    g.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(_as_u64(out), oracle.pospopcnt(words, 16))
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads (2 GiB each), in the launch configuration the
+# benchmark times
+
+def _full(width, words, offset=0, kernels=("auto", "csa", "tma")):
+    _, x = _device_slice(words, offset)
+    ref, _ = oracle.pospopcnt_mt(words, width)
+    for k in kernels:
+        out = torch.empty(width, dtype=torch.int64, device="cuda")
+        if k == "auto":
+            run_kernel(width, None, x, out)
+        else:
+            run_kernel(width, k, x, out)
+        torch.cuda.synchronize()
+        assert np.array_equal(_as_u64(out), ref), k
+    del x
+    torch.cuda.empty_cache()
+    return ref
+
+
+@pytest.mark.slow
+def test_full_u16_uniform():
+    _full(16, synth.uniform_bits(0, 1 << 30, 16))
+
+
+@pytest.mark.slow
+def test_full_u16_one_hot_zipf():
+    w, pos = synth.one_hot(0, 1 << 30, 16, return_positions=True)
+    ref = _full(16, w)
+    assert int(ref.sum()) == 1 << 30
+    assert np.array_equal(ref, np.bincount(pos, minlength=16).astype(np.uint64))
+
+
+@pytest.mark.slow
+def test_full_u16_sparse():
+    _full(16, synth.sparse(0, 1 << 30, 16))
+
+
+@pytest.mark.slow
+def test_full_u16_misaligned_ragged():
+    """n = 2^30 + 7 words starting 2 bytes past a 256-byte boundary."""
+    _full(16, synth.uniform_bits(1, (1 << 30) + 7, 16), offset=2)
+
+
+@pytest.mark.slow
+def test_full_u8_u32():
+    for width, n in ((8, 1 << 31), (32, 1 << 29)):
+        ref = _full(width, synth.one_hot(0, n, width, cdf=synth.uniform_cdf(width)), kernels=("auto",))
+        assert int(ref.sum()) == n
+        _full(width, synth.uniform_bits(0, n, width), kernels=("auto",))
