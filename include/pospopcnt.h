@@ -126,6 +126,25 @@ int pospopcnt_count_host(int width, const void* h_in, size_t n, uint64_t* h_coun
 int pospopcnt_batched(const void* d_in, const int64_t* d_offsets, size_t nseg, int width,
                       uint64_t* d_counts, cudaStream_t stream);
 
+/* pospopcnt_batched for callers that cannot allocate device memory (their
+ * memory belongs to another runtime's pool allocator, or they must not
+ * allocate once running).  The paper has no counterpart: this is a property
+ * of the library, not of the method.  Same arguments, layout and result as
+ * pospopcnt_batched; it calls no cudaMalloc, cudaFree or other allocating
+ * routine, and needs no pospopcnt_init.  Its scratch (the work-queue state
+ * of one launch, 16 bytes) is a 256-byte static device array that every GPU
+ * which loads the library holds until the process exits; a call whose
+ * scratch need exceeded 256 bytes would be rejected with
+ * POSPOPCNT_ERR_TOO_LARGE (the need does not grow with the input, so every
+ * input size fits).  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current): make that first
+ * call before any stream capture.  Every call on a device shares the one
+ * array and clears it on its stream before launching, so calls that overlap
+ * on the GPU (other streams, concurrent graph replays) race and give wrong
+ * counts: serialise them. */
+int pospopcnt_batched_noalloc(const void* d_in, const int64_t* d_offsets, size_t nseg, int width,
+                              uint64_t* d_counts, cudaStream_t stream);
+
 /* The per-segment alternative to pospopcnt_batched, for offsets known on
  * the host: one plain count (memset + kernel) per segment, issued in order
  * on `stream` from a host loop.  h_offsets: nseg+1 int64 word offsets in

@@ -23,7 +23,7 @@ from . import _build
 __all__ = [
     "PospopcntError", "load", "pospopcnt_init", "pospopcnt_u8", "pospopcnt_u16", "pospopcnt_u32",
     "pospopcnt_count", "pospopcnt_count_config", "pospopcnt_count_accumulate", "pospopcnt_count_host",
-    "pospopcnt_batched", "pospopcnt_plain_segments", "pospopcnt_check_device_error", "pospopcnt_plan_split",
+    "pospopcnt_batched", "pospopcnt_batched_noalloc", "pospopcnt_plain_segments", "pospopcnt_check_device_error", "pospopcnt_plan_split",
     "pospopcnt_get_config", "pospopcnt_set_config", "pospopcnt_autotune", "pospopcnt_strerror",
     "pospopcnt_last_cuda_error", "pospopcnt_launch_count", "pospopcnt_selftest_timeout", "KERNELS",
     "Config",
@@ -89,6 +89,7 @@ def _declare(lib):
         "pospopcnt_count_host": (i32, [i32, vp, sz, vp]),
         "pospopcnt_batched": (i32, [vp, vp, sz, i32, vp, vp]),
         "pospopcnt_plain_segments": (i32, [vp, vp, sz, i32, vp, vp]),
+        "pospopcnt_batched_noalloc": (i32, [vp, vp, sz, i32, vp, vp]),
         "pospopcnt_check_device_error": (i32, [vp]),
         "pospopcnt_plan_split": (i32, [i32, u64, sz, P(sz), P(sz), P(sz)]),
         "pospopcnt_get_config": (i32, [i32, sz, P(Config)]),
@@ -251,6 +252,22 @@ def pospopcnt_batched(x, offsets, width: int, counts=None, stream=None):
     with torch.cuda.device(x.device):
         _check(_lib().pospopcnt_batched(ptr, offsets.data_ptr(), nseg, width, out.data_ptr(),
                                         _stream_handle(stream, x.device)), "pospopcnt_batched")
+    return out
+
+
+def pospopcnt_batched_noalloc(x, offsets, width: int, counts, stream=None):
+    """pospopcnt_batched that allocates nothing (see the C header): the
+    caller passes the output rows; the library uses only a static device
+    array as scratch, shared by every call on the device."""
+    torch = _torch()
+    ptr, _ = _words(x, width)
+    if offsets.dtype != torch.int64 or not offsets.is_cuda or not offsets.is_contiguous():
+        raise ValueError("offsets must be a contiguous CUDA int64 tensor")
+    nseg = max(offsets.numel() - 1, 0)
+    out = _counts_out(counts, width, nseg, x.device)
+    with torch.cuda.device(x.device):
+        _check(_lib().pospopcnt_batched_noalloc(ptr, offsets.data_ptr(), nseg, width, out.data_ptr(),
+                                                _stream_handle(stream, x.device)), "pospopcnt_batched_noalloc")
     return out
 
 

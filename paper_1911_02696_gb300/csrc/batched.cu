@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "device_common.cuh"
 #include "internal.h"
@@ -185,3 +186,92 @@ int launch_batched(const DeviceState& st, const void* d_in, const int64_t* d_off
 }
 
 }  // namespace ppc
+
+// ---------------------------------------------------------------------------
+// Allocation-free form of the batched count.
+//
+// Some callers cannot call cudaMalloc: a host process whose device memory
+// is owned by another runtime's pool allocator (which must see every
+// allocation), code that must not allocate once it has started (a
+// latency-critical or memory-capped service), or an embedding that forbids
+// third-party libraries from allocating at all.  pospopcnt_batched and the
+// other entry points allocate the library workspace on their first call;
+// pospopcnt_batched_noalloc never does.  The only scratch the batched
+// kernel needs -- the work-queue state of one launch -- lives in the static
+// array below, which every GPU that loads this library holds until the
+// process exits.
+//
+// In host code g_noalloc_scratch names a host-side stand-in, not a device
+// address: the device address is looked up with cudaGetSymbolAddress once
+// per device (on that device's first call, with the device current) and
+// passed to the kernel.
+
+namespace ppc {
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = 256;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+int g_noalloc_sms[NOALLOC_MAX_DEVICES] = {};
+}  // namespace
+
+}  // namespace ppc
+
+extern "C" int pospopcnt_batched_noalloc(const void* d_in, const int64_t* d_offsets, size_t nseg, int width,
+                                         uint64_t* d_counts, cudaStream_t stream) {
+  using namespace ppc;
+  if (width != 8 && width != 16 && width != 32) return POSPOPCNT_ERR_INVALID;
+  if (nseg == 0) return POSPOPCNT_OK;
+  if (!d_in || !d_offsets || !d_counts) return POSPOPCNT_ERR_INVALID;
+  if (reinterpret_cast<uintptr_t>(d_in) % uintptr_t(width / 8) != 0) return POSPOPCNT_ERR_MISALIGNED;
+  if (reinterpret_cast<uintptr_t>(d_offsets) % 8 != 0 || reinterpret_cast<uintptr_t>(d_counts) % 8 != 0)
+    return POSPOPCNT_ERR_MISALIGNED;
+  if (nseg > (size_t(1) << 40)) return POSPOPCNT_ERR_TOO_LARGE;
+  // scratch one launch needs: the queue state (fixed, independent of the input)
+  const size_t need = sizeof(QueueSlot);
+  if (need > NOALLOC_SCRATCH_BYTES) return POSPOPCNT_ERR_TOO_LARGE;
+
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return POSPOPCNT_ERR_NOT_INITIALIZED;
+  void* scratch = nullptr;
+  int sms = 0;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {  // set-up, once per device, with that device current
+      void* p = nullptr;
+      if ((e = cudaGetSymbolAddress(&p, g_noalloc_scratch)) != cudaSuccess) return cuda_fail(e);
+      int n = 0;
+      if ((e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return cuda_fail(e);
+      if (!p || n <= 0) return POSPOPCNT_ERR_NOT_INITIALIZED;
+      g_noalloc_sms[dev] = n;
+      g_noalloc_ptr[dev] = p;
+    }
+    scratch = g_noalloc_ptr[dev];
+    sms = g_noalloc_sms[dev];
+  }
+  // The array keeps the previous call's contents: the queue state must start
+  // at zero, and the rows are overwritten.
+  if ((e = cudaMemsetAsync(scratch, 0, need, stream)) != cudaSuccess) return cuda_fail(e);
+  if ((e = cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * size_t(width) * nseg, stream)) != cudaSuccess)
+    return cuda_fail(e);
+  DeviceState st;
+  st.sms = sms;
+  BatchedArgs a;
+  a.base = static_cast<const uint8_t*>(d_in);
+  a.offsets = d_offsets;
+  a.nseg = nseg;
+  a.counts = reinterpret_cast<unsigned long long*>(d_counts);
+  a.q = static_cast<QueueSlot*>(scratch);
+  a.tile_words = uint64_t((128 * 1024) / (width / 8));
+  switch (width) {
+    case 8: return launch_batched_k<8>(st, a, stream);
+    case 16: return launch_batched_k<16>(st, a, stream);
+    default: return launch_batched_k<32>(st, a, stream);
+  }
+}
