@@ -52,10 +52,14 @@ def peak_hbm():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def csrc_hash():
+KERNEL_SOURCES = ("device_common.cuh", "plain_kernels.cuh")
+
+
+def csrc_hash(files=KERNEL_SOURCES):
+    """Hash of the sources that define the single-stream kernels."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1911_02696_gb300", "csrc")
-    for name in sorted(os.listdir(d)):
+    for name in files:
         with open(os.path.join(d, name), "rb") as f:
             h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
