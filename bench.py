@@ -353,6 +353,7 @@ def run_sweep(args, world, rank, local):
             for _ in range(reps):
                 if mode == "cold" and nbytes <= l2:
                     flush.fill_(1)
+                torch.cuda._sleep(200000)  # GPU busy while the host enqueues: events see device time only
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(stream)
                 ppc.pospopcnt_u16(x, counts=counts)
@@ -451,6 +452,88 @@ def run_batched(args, world, rank, local):
             "speedup_vs_plain": round(plain_ms / batched_ms, 2)}
 
 
+def candidate_configs():
+    cfgs = [dict(kernel="csa", threads=t, unroll=u) for t in (128, 256, 512) for u in (2, 4, 8)]
+    cfgs += [dict(kernel="tma", stages=st, chunk_bytes=c) for st in (2, 3, 4, 6, 8)
+             for c in (16384, 32768, 65536) if st * c <= 196608]
+    cfgs += [dict(kernel="ballot", unroll=u) for u in (1, 2, 4)]
+    return cfgs
+
+
+def run_kernels(args, world, rank, local):
+    """Every launch configuration of every kernel family on the 2 GiB
+    uniform-bits input of each width (u8 2^31, u16 2^30, u32 2^29 words),
+    plus the autotuner's pick."""
+    import torch
+    import paper_1911_02696_gb300 as ppc
+    import synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ppc.pospopcnt_init(local)
+    stream = torch.cuda.current_stream(dev)
+    x = torch.from_numpy(synth.uniform_bytes(rank, 1 << 31)).to(dev)
+    peak, _ = peak_hbm()
+    table = {}
+    steps = max(5, min(args.steps, 50))
+    for width in (8, 16, 32):
+        counts = torch.empty(width, dtype=torch.int64, device=dev)
+        ref = None
+        rows = []
+        for cfg in candidate_configs():
+            for _ in range(args.warmup):
+                ppc.pospopcnt_count_config(width, cfg, x, counts=counts)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(steps):
+                ppc.pospopcnt_count_config(width, cfg, x, counts=counts)
+            b.record(stream)
+            b.synchronize()
+            ms = a.elapsed_time(b) / steps
+            got = counts.cpu().numpy().copy()
+            ref = got if ref is None else ref
+            assert np.array_equal(got, ref), ("configs disagree", width, cfg)
+            gbs = (1 << 31) / (ms * 1e-3) / 1e9
+            rows.append({**cfg, "ms": round(ms, 4), "GBps": round(gbs, 1), "frac": round(gbs / peak, 4)})
+        best, best_ms = ppc.pospopcnt_autotune(width, x, counts)
+        table[f"u{width}"] = {"configs": rows, "autotune": {**best, "ms": round(best_ms, 4),
+                                                            "GBps": round((1 << 31) / (best_ms * 1e-3) / 1e9, 1)}}
+    if rank != 0:
+        return None
+    top = max(r["GBps"] for r in table["u16"]["configs"])
+    return {"metric": "pospopcnt GB/s per kernel configuration", "value": top, "unit": UNIT, "n_gpus": world,
+            "steps": steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8/u16/u32", "data": "synthetic",
+            "config": {"workload": "2 GiB uniform random bits per width", "peak_GBps": peak}, "table": table}
+
+
+def run_autotune(args, world, rank, local):
+    """The library's autotuner at every size class from 64 KiB to 4 GiB for
+    each width (prefixes of one 4 GiB uniform-bits buffer)."""
+    import torch
+    import paper_1911_02696_gb300 as ppc
+    import synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ppc.pospopcnt_init(local)
+    x = torch.from_numpy(synth.uniform_bytes(rank, 4 << 30)).to(dev)
+    table = {}
+    for width in (8, 16, 32):
+        counts = torch.empty(width, dtype=torch.int64, device=dev)
+        rows = []
+        for e in range(8, 17):
+            nbytes = 1 << (2 * e)
+            best, ms = ppc.pospopcnt_autotune(width, x[:nbytes], counts)
+            rows.append({"size_class": e, "bytes": nbytes, **best, "ms": round(ms, 5),
+                         "GBps": round(nbytes / (ms * 1e-3) / 1e9, 1)})
+        table[f"u{width}"] = rows
+    if rank != 0:
+        return None
+    return {"metric": "autotuned configuration per size class", "value": None, "unit": UNIT, "n_gpus": world,
+            "steps": 5, "warmup": 2, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u8/u16/u32", "data": "synthetic", "config": {"workload": "prefixes of 4 GiB uniform bits"},
+            "table": table}
+
+
 def run_reference(args, world, rank):
     """The reference arm: the scalar CPU oracle on the host cores, each step
     a bounded 2^26-word sample of the same workload."""
@@ -488,7 +571,8 @@ def main(argv=None):
     p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="u16",
-                   choices=["u16", "u16_onehot", "u16_sparse", "u16_misaligned", "u8", "u32", "sweep", "batched"])
+                   choices=["u16", "u16_onehot", "u16_sparse", "u16_misaligned", "u8", "u32", "sweep", "batched",
+                            "kernels", "autotune"])
     p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--log2-words", type=int, default=None,
                    help="run a smaller uniform-bits case of 2^k words (profiling only)")
@@ -509,6 +593,10 @@ def main(argv=None):
             out = run_sweep(args, world, rank, local)
         elif args.workload == "batched":
             out = run_batched(args, world, rank, local)
+        elif args.workload == "kernels":
+            out = run_kernels(args, world, rank, local)
+        elif args.workload == "autotune":
+            out = run_autotune(args, world, rank, local)
         else:
             out = run_plain(args, world, rank, local)
         if world > 1:

@@ -47,10 +47,43 @@ pospopcnt_config default_config() {
   return c;
 }
 
+// Defaults per width and size class (floor(log4 bytes)), from the library's
+// autotuner run on a GB300 (152 SMs, 2070 MHz): below 256 KiB one wide CTA
+// (512 threads x 8 vectors covers 64 KiB in one trip, and a one-CTA grid
+// stores its counts without a memset); up to 64 MiB the register-load CSA
+// kernel; from 64 MiB (u16, u32) the bulk-copy ring, 3 stages x 64 KiB from
+// 256 MiB; u8 keeps the CSA kernel with 512-thread CTAs (its flush is the
+// cheapest, and the register path measured fastest at 1-4 GiB).
+pospopcnt_config tuned_default(int width, int cls) {
+  pospopcnt_config c = default_config();
+  if (cls <= 8) {
+    c.threads = 512, c.unroll = 8;
+    return c;
+  }
+  if (cls <= 11) {
+    c.threads = 128, c.unroll = 4;
+    return c;
+  }
+  if (width == 8) {
+    c.threads = cls >= 13 ? 512 : 256;
+    c.unroll = 4;
+    return c;
+  }
+  if (cls == 12) {
+    c.threads = 128, c.unroll = 8;
+    return c;
+  }
+  c.kernel = POSPOPCNT_KERNEL_TMA;
+  c.stages = cls == 13 ? 2 : 3;
+  c.chunk_bytes = cls == 13 ? 32768 : 65536;
+  return c;
+}
+
 void init_configs(int dev) {
   if (g_cfg_ready[dev]) return;
+  const int widths[3] = {8, 16, 32};
   for (int w = 0; w < 3; ++w)
-    for (int c = 0; c < NCLASSES; ++c) g_cfg[dev][w][c] = default_config();
+    for (int c = 0; c < NCLASSES; ++c) g_cfg[dev][w][c] = tuned_default(widths[w], c);
   g_cfg_ready[dev] = true;
 }
 
@@ -161,15 +194,15 @@ int normalize_config(const DeviceState& st, int width, pospopcnt_config* c) {
 }
 
 template <int K>
-int launch_plain_k(const DeviceState&, const pospopcnt_config&, const void*, size_t, unsigned long long*,
+int launch_plain_k(const DeviceState&, const pospopcnt_config&, const void*, size_t, unsigned long long*, bool,
                    cudaStream_t);
 
 int launch_plain(const DeviceState& st, int width, const pospopcnt_config& cfg, const void* d_in, size_t n,
-                 unsigned long long* d_counts, cudaStream_t stream) {
+                 unsigned long long* d_counts, bool zero_first, cudaStream_t stream) {
   switch (width) {
-    case 8: return launch_plain_k<8>(st, cfg, d_in, n, d_counts, stream);
-    case 16: return launch_plain_k<16>(st, cfg, d_in, n, d_counts, stream);
-    case 32: return launch_plain_k<32>(st, cfg, d_in, n, d_counts, stream);
+    case 8: return launch_plain_k<8>(st, cfg, d_in, n, d_counts, zero_first, stream);
+    case 16: return launch_plain_k<16>(st, cfg, d_in, n, d_counts, zero_first, stream);
+    case 32: return launch_plain_k<32>(st, cfg, d_in, n, d_counts, zero_first, stream);
   }
   return POSPOPCNT_ERR_INVALID;
 }
@@ -197,12 +230,7 @@ int count_impl(int width, const pospopcnt_config* cfg_in, bool zero, const void*
   if (!st) return rc;
   pospopcnt_config cfg = cfg_in ? *cfg_in : config_for(*st, width, n);
   if ((rc = normalize_config(*st, width, &cfg)) != POSPOPCNT_OK) return rc;
-  if (zero) {
-    const cudaError_t e = cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * size_t(width), stream);
-    if (e != cudaSuccess) return cuda_fail(e);
-  }
-  if (n == 0) return POSPOPCNT_OK;
-  return launch_plain(*st, width, cfg, d_in, n, reinterpret_cast<unsigned long long*>(d_counts), stream);
+  return launch_plain(*st, width, cfg, d_in, n, reinterpret_cast<unsigned long long*>(d_counts), zero, stream);
 }
 
 }  // namespace
@@ -284,7 +312,7 @@ int pospopcnt_count_host(int width, const void* h_in, size_t n, uint64_t* h_coun
     void* buf = st->d_stage[j & 1];
     if ((e = cudaMemcpyAsync(buf, src + done * wb, words * wb, cudaMemcpyHostToDevice, s)) != cudaSuccess)
       return cuda_fail(e);
-    if ((rc = launch_plain(*st, width, cfg, buf, words, st->d_acc, s)) != POSPOPCNT_OK) return rc;
+    if ((rc = launch_plain(*st, width, cfg, buf, words, st->d_acc, false, s)) != POSPOPCNT_OK) return rc;
     done += words;
   }
   if ((e = cudaEventRecord(st->hevent[1], s1)) != cudaSuccess) return cuda_fail(e);

@@ -41,6 +41,11 @@ struct BatchedArgs {
 
 constexpr int BT_THREADS = 256;
 constexpr int BT_WARPS = BT_THREADS / 32;
+// resident CTAs per SM the kernel is compiled for (register cap 65536 / (256 x this))
+template <int K>
+struct bt_min_blocks {
+  static constexpr int value = K == 32 ? 3 : 5;
+};
 
 // Largest s in [0, nseg) with offsets[s] <= w (requires offsets[0] <= w <
 // offsets[nseg]).  Each round the 32 lanes probe 32 evenly spaced candidates.
@@ -77,8 +82,15 @@ __device__ __forceinline__ void warp_count_piece(const uint8_t* base, uint64_t p
   uint64_t bodyE = E & ~uint64_t(15);
   if (bodyE < bodyA) bodyE = bodyA;
   const uint64_t nvec = (bodyE - bodyA) / 16;
+  // lanes 0..14 take the head words, lanes 16..30 the tail words (<= 15 each);
+  // loaded before the body loop so only this word stays live across it
   const uint32_t head_words = uint32_t((bodyA - A) / WB);
   const uint32_t tail_words = uint32_t((E - bodyE) / WB);
+  uint32_t edge = 0;
+  if (uint32_t(lane) < head_words)
+    edge = load_word<K>(reinterpret_cast<const uint8_t*>(A) + lane * WB);
+  else if (lane >= 16 && uint32_t(lane - 16) < tail_words)
+    edge = load_word<K>(reinterpret_cast<const uint8_t*>(bodyE) + (lane - 16) * WB);
 
   uint32_t B[4] = {0, 0, 0, 0};
   uint32_t top[K];
@@ -97,16 +109,13 @@ __device__ __forceinline__ void warp_count_piece(const uint8_t* base, uint64_t p
   }
   uint32_t c[K];
   finalize<K, 4>(c, top, B);
-  if (uint32_t(lane) < head_words)
-    count_word<K>(c, load_word<K>(reinterpret_cast<const uint8_t*>(A) + lane * WB));
-  if (lane >= 16 && uint32_t(lane - 16) < tail_words)
-    count_word<K>(c, load_word<K>(reinterpret_cast<const uint8_t*>(bodyE) + (lane - 16) * WB));
+  count_word<K>(c, edge);
   const uint32_t v = warp_reduce_positions<K>(c);
   if ((lane & ((1 << SH) - 1)) == 0 && v) atomicAdd(row + (lane >> SH), (unsigned long long)v);
 }
 
 template <int K>
-__global__ void __launch_bounds__(BT_THREADS) batched_kernel(BatchedArgs a) {
+__global__ void __launch_bounds__(BT_THREADS, bt_min_blocks<K>::value) batched_kernel(BatchedArgs a) {
   constexpr int WB = K / 8;
   __shared__ unsigned long long s_tile;
   const int warp = threadIdx.x >> 5;

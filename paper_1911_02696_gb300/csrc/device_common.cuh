@@ -149,10 +149,13 @@ __device__ __forceinline__ uint32_t warp_reduce_positions(uint32_t (&v)[K]) {
   return v[0];
 }
 
-// Block reduction followed by one 64-bit atomic add per position per block.
-// Every thread of the block must call it.
+// Block reduction followed by one 64-bit atomic add per position per block,
+// or, when the block is the whole grid and the caller asked for it (store),
+// a plain store of every position (no prior memset needed).  Every thread of
+// the block must call it.
 template <int K, int NWARPS>
-__device__ __forceinline__ void block_reduce_add(uint32_t (&c)[K], unsigned long long* counts) {
+__device__ __forceinline__ void block_reduce_add(uint32_t (&c)[K], unsigned long long* counts,
+                                                 bool store = false) {
   __shared__ uint32_t red[NWARPS][K];
   constexpr int SH = 5 - ilog2<K>::value;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -163,7 +166,10 @@ __device__ __forceinline__ void block_reduce_add(uint32_t (&c)[K], unsigned long
     unsigned long long s = 0;
 #pragma unroll
     for (int w = 0; w < NWARPS; ++w) s += red[w][threadIdx.x];
-    if (s) atomicAdd(counts + threadIdx.x, s);
+    if (store)
+      counts[threadIdx.x] = s;
+    else if (s)
+      atomicAdd(counts + threadIdx.x, s);
   }
 }
 

@@ -46,9 +46,11 @@ struct Split {
 };
 Split plan_split(int width, uint64_t addr, size_t n);
 
-// Launch of one single-stream count (no memset; adds into d_counts).
+// Launch of one single-stream count.  zero_first: the counts are
+// overwritten (memset + atomics, or a direct store by a one-CTA grid);
+// otherwise the kernel adds into d_counts.
 int launch_plain(const DeviceState& st, int width, const pospopcnt_config& cfg, const void* d_in,
-                 size_t n, unsigned long long* d_counts, cudaStream_t stream);
+                 size_t n, unsigned long long* d_counts, bool zero_first, cudaStream_t stream);
 
 // Validates a configuration for a width; fills defaults for zero fields.
 int normalize_config(const DeviceState& st, int width, pospopcnt_config* cfg);

@@ -35,6 +35,7 @@ struct PlainArgs {
   uint32_t tail_words;
   unsigned long long* counts;
   unsigned* err;
+  uint32_t store;  // 1: single-CTA grid writes the counts (no memset, no atomics)
 };
 
 template <int K, int NTHREADS>
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(NTHREADS) csa_kernel(PlainArgs a) {
   uint32_t c[K];
   finalize<K, L>(c, top, B);
   count_head_tail<K, NTHREADS>(c, a);
-  block_reduce_add<K, NTHREADS / 32>(c, a.counts);
+  block_reduce_add<K, NTHREADS / 32>(c, a.counts, a.store != 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -211,7 +212,7 @@ __global__ void __launch_bounds__(TMA_THREADS) tma_kernel(TmaArgs a) {
     }
   }
   count_head_tail<K, TMA_THREADS>(c, a.p);
-  block_reduce_add<K, TMA_CWARPS + 1>(c, a.p.counts);
+  block_reduce_add<K, TMA_CWARPS + 1>(c, a.p.counts, a.p.store != 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -240,7 +241,7 @@ __global__ void __launch_bounds__(NTHREADS) ballot_kernel(PlainArgs a) {
 #pragma unroll
   for (int p = 0; p < K; ++p) c[p] = lane == 0 ? acc[p] : 0u;  // every lane holds the warp total
   count_head_tail<K, NTHREADS>(c, a);
-  block_reduce_add<K, NTHREADS / 32>(c, a.counts);
+  block_reduce_add<K, NTHREADS / 32>(c, a.counts, a.store != 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -258,14 +259,27 @@ static int occupancy(Kern kern, int threads, size_t smem) {
 // 2^31 bytes.
 static inline uint64_t min_blocks_for(uint64_t nbytes) { return (nbytes >> 31) + 1; }
 
+// Overwrite semantics: a one-CTA grid stores its counts; a larger grid adds
+// atomically into counts zeroed first by a stream-ordered memset.
+template <int K>
+static int prepare_counts(PlainArgs& a, uint64_t grid, bool zero_first, cudaStream_t stream) {
+  a.store = (zero_first && grid == 1) ? 1u : 0u;
+  if (zero_first && grid > 1) {
+    const cudaError_t e = cudaMemsetAsync(a.counts, 0, sizeof(unsigned long long) * K, stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  return POSPOPCNT_OK;
+}
+
 template <int K, int U, int T>
-static int launch_csa(const DeviceState& st, const PlainArgs& a, int bps, cudaStream_t stream) {
+static int launch_csa(const DeviceState& st, PlainArgs a, int bps, bool zero_first, cudaStream_t stream) {
   auto kern = csa_kernel<K, U, T>;
   const int occ = occupancy(kern, T, 0);
   const uint64_t cap = uint64_t(st.sms) * uint64_t(std::min(bps > 0 ? bps : occ, occ));
   const uint64_t need = (a.nvec + uint64_t(U) * T - 1) / (uint64_t(U) * T);
   uint64_t grid = std::max<uint64_t>(1, std::min(cap, need));
   grid = std::max(grid, min_blocks_for(a.nvec * 16));
+  if (const int rc = prepare_counts<K>(a, grid, zero_first, stream)) return rc;
   kern<<<unsigned(grid), T, 0, stream>>>(a);
   note_launch();
   const cudaError_t e = cudaGetLastError();
@@ -273,7 +287,7 @@ static int launch_csa(const DeviceState& st, const PlainArgs& a, int bps, cudaSt
 }
 
 template <int K, int U, int T>
-static int launch_ballot(const DeviceState& st, const PlainArgs& a, int bps, cudaStream_t stream) {
+static int launch_ballot(const DeviceState& st, PlainArgs a, int bps, bool zero_first, cudaStream_t stream) {
   auto kern = ballot_kernel<K, U, T>;
   const int occ = occupancy(kern, T, 0);
   const uint64_t cap = uint64_t(st.sms) * uint64_t(std::min(bps > 0 ? bps : occ, occ));
@@ -281,6 +295,7 @@ static int launch_ballot(const DeviceState& st, const PlainArgs& a, int bps, cud
   const uint64_t need = (a.nvec + per - 1) / per;
   uint64_t grid = std::max<uint64_t>(1, std::min(cap, need));
   grid = std::max(grid, min_blocks_for(a.nvec * 16));
+  if (const int rc = prepare_counts<K>(a, grid, zero_first, stream)) return rc;
   kern<<<unsigned(grid), T, 0, stream>>>(a);
   note_launch();
   const cudaError_t e = cudaGetLastError();
@@ -288,7 +303,7 @@ static int launch_ballot(const DeviceState& st, const PlainArgs& a, int bps, cud
 }
 
 template <int K>
-static int launch_tma(const DeviceState& st, const PlainArgs& p, int bps, int stages, int chunk,
+static int launch_tma(const DeviceState& st, const PlainArgs& p, int bps, int stages, int chunk, bool zero_first,
                       cudaStream_t stream) {
   auto kern = tma_kernel<K>;
   const size_t smem = size_t(stages) * size_t(chunk);
@@ -305,6 +320,7 @@ static int launch_tma(const DeviceState& st, const PlainArgs& p, int bps, int st
   const uint64_t nchunks = (a.body_bytes + chunk - 1) / chunk;
   uint64_t grid = std::max<uint64_t>(1, std::min(cap, nchunks));
   grid = std::max(grid, std::min<uint64_t>(nchunks, min_blocks_for(a.body_bytes)));
+  if (const int rc = prepare_counts<K>(a.p, grid, zero_first, stream)) return rc;
   kern<<<unsigned(grid), TMA_THREADS, smem, stream>>>(a);
   note_launch();
   const cudaError_t e = cudaGetLastError();
@@ -312,19 +328,19 @@ static int launch_tma(const DeviceState& st, const PlainArgs& p, int bps, int st
 }
 
 template <int K, int T>
-static int launch_csa_u(const DeviceState& st, const PlainArgs& a, const pospopcnt_config& cfg,
+static int launch_csa_u(const DeviceState& st, const PlainArgs& a, const pospopcnt_config& cfg, bool zero_first,
                         cudaStream_t stream) {
   switch (cfg.unroll) {
-    case 2: return launch_csa<K, 2, T>(st, a, cfg.blocks_per_sm, stream);
-    case 4: return launch_csa<K, 4, T>(st, a, cfg.blocks_per_sm, stream);
-    case 8: return launch_csa<K, 8, T>(st, a, cfg.blocks_per_sm, stream);
+    case 2: return launch_csa<K, 2, T>(st, a, cfg.blocks_per_sm, zero_first, stream);
+    case 4: return launch_csa<K, 4, T>(st, a, cfg.blocks_per_sm, zero_first, stream);
+    case 8: return launch_csa<K, 8, T>(st, a, cfg.blocks_per_sm, zero_first, stream);
   }
   return POSPOPCNT_ERR_INVALID;
 }
 
 template <int K>
 int launch_plain_k(const DeviceState& st, const pospopcnt_config& cfg, const void* d_in, size_t n,
-                   unsigned long long* d_counts, cudaStream_t stream) {
+                   unsigned long long* d_counts, bool zero_first, cudaStream_t stream) {
   const Split sp = plan_split(K, reinterpret_cast<uint64_t>(d_in), n);
   const uint8_t* base = static_cast<const uint8_t*>(d_in);
   PlainArgs a;
@@ -336,23 +352,28 @@ int launch_plain_k(const DeviceState& st, const pospopcnt_config& cfg, const voi
   a.tail_words = uint32_t(sp.tail_words);
   a.counts = d_counts;
   a.err = st.d_err;
-  if (a.nvec == 0 && a.head_words == 0 && a.tail_words == 0) return POSPOPCNT_OK;
+  a.store = 0;
+  if (a.nvec == 0 && a.head_words == 0 && a.tail_words == 0) {
+    if (!zero_first) return POSPOPCNT_OK;
+    const cudaError_t e = cudaMemsetAsync(d_counts, 0, sizeof(unsigned long long) * K, stream);
+    return e == cudaSuccess ? POSPOPCNT_OK : cuda_fail(e);
+  }
   switch (cfg.kernel) {
     case POSPOPCNT_KERNEL_CSA:
       switch (cfg.threads) {
-        case 128: return launch_csa_u<K, 128>(st, a, cfg, stream);
-        case 256: return launch_csa_u<K, 256>(st, a, cfg, stream);
-        case 512: return launch_csa_u<K, 512>(st, a, cfg, stream);
+        case 128: return launch_csa_u<K, 128>(st, a, cfg, zero_first, stream);
+        case 256: return launch_csa_u<K, 256>(st, a, cfg, zero_first, stream);
+        case 512: return launch_csa_u<K, 512>(st, a, cfg, zero_first, stream);
       }
       return POSPOPCNT_ERR_INVALID;
     case POSPOPCNT_KERNEL_TMA:
-      if (a.nvec == 0) return launch_csa<K, 4, 256>(st, a, 1, stream);  // head/tail only
-      return launch_tma<K>(st, a, cfg.blocks_per_sm, cfg.stages, cfg.chunk_bytes, stream);
+      if (a.nvec == 0) return launch_csa<K, 4, 256>(st, a, 1, zero_first, stream);  // head/tail only
+      return launch_tma<K>(st, a, cfg.blocks_per_sm, cfg.stages, cfg.chunk_bytes, zero_first, stream);
     case POSPOPCNT_KERNEL_BALLOT:
       switch (cfg.unroll) {
-        case 1: return launch_ballot<K, 1, 256>(st, a, cfg.blocks_per_sm, stream);
-        case 2: return launch_ballot<K, 2, 256>(st, a, cfg.blocks_per_sm, stream);
-        case 4: return launch_ballot<K, 4, 256>(st, a, cfg.blocks_per_sm, stream);
+        case 1: return launch_ballot<K, 1, 256>(st, a, cfg.blocks_per_sm, zero_first, stream);
+        case 2: return launch_ballot<K, 2, 256>(st, a, cfg.blocks_per_sm, zero_first, stream);
+        case 4: return launch_ballot<K, 4, 256>(st, a, cfg.blocks_per_sm, zero_first, stream);
       }
       return POSPOPCNT_ERR_INVALID;
   }

@@ -247,3 +247,20 @@ def test_full_u8_u32():
         ref = _full(width, synth.one_hot(0, n, width, cdf=synth.uniform_cdf(width)), kernels=("auto",))
         assert int(ref.sum()) == n
         _full(width, synth.uniform_bits(0, n, width), kernels=("auto",))
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_overwrite_across_grid_sizes(width):
+    """Counts are overwritten whether the grid is one CTA (direct store, no
+    memset) or many (memset + atomics): sizes around the one-CTA limits of
+    every default configuration, counts pre-filled with garbage."""
+    wb = width // 8
+    for nbytes in (wb, 1008, 4096, 16384, 65536 - 16, 65536, 65536 + 16, 131072 + 2 * wb, 262144 + 4 * wb,
+                   (4 << 20) + 8, (16 << 20) + 4 * wb, (64 << 20) + 16):
+        n = nbytes // wb
+        words = synth.uniform_bits(nbytes, n, width)
+        _, x = _device_slice(words, 0)
+        out = torch.randint(-2 ** 62, 2 ** 62, (width,), dtype=torch.int64, device="cuda")
+        run_kernel(width, None, x, out)
+        torch.cuda.synchronize()
+        assert np.array_equal(_as_u64(out), oracle.pospopcnt(words, width)), nbytes
