@@ -534,6 +534,82 @@ def run_autotune(args, world, rank, local):
             "table": table}
 
 
+def run_serve(args, world, rank, local):
+    """Serving: open-loop Poisson arrivals (50k req/s by default) of requests
+    with width 8/16/32 (weights 0.2/0.6/0.2) and payloads log-uniform in
+    1 KiB..256 MiB, each a slice of a 4 GiB device pool of uniform random
+    bits, HBM admission budget 64 GiB.  The same trace is served by the
+    continuous-batching runtime and by per-request plain launches; latency
+    = completion seen on the host - scheduled arrival."""
+    import torch
+    import paper_1911_02696_gb300 as ppc
+    import synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ppc.pospopcnt_init(local)
+    pool_bytes = 4 << 30
+    pool = torch.from_numpy(synth.uniform_bytes(100 + rank, pool_bytes)).to(dev)
+    tr = synth.serving_trace(rank, rate=args.serve_rate, duration=args.serve_seconds, pool_bytes=pool_bytes)
+    n = tr["t_arrival"].size
+    wb = (tr["width"] // 8).astype(np.uint64)
+    nbytes = tr["nwords"] * wb
+    addr = np.uint64(pool.data_ptr()) + tr["offset_bytes"].astype(np.uint64)
+    total = int(nbytes.sum())
+
+    def serve(per_request):
+        srv = ppc.pospopcnt_server_create(local, hbm_budget_bytes=64 << 30, per_request=per_request,
+                                          max_inflight=64 if per_request else 4,
+                                          max_batch_jobs=1 if per_request else 4096)
+        try:
+            # warm-up: a short slice of the trace
+            k = min(n, 2000)
+            ppc.pospopcnt_server_run_trace(srv, tr["t_arrival"][:k] - tr["t_arrival"][0], tr["width"][:k],
+                                           addr[:k], tr["nwords"][:k])
+            t0 = time.perf_counter()
+            lat, counts, status = ppc.pospopcnt_server_run_trace(srv, tr["t_arrival"], tr["width"], addr,
+                                                                 tr["nwords"], want_counts=True)
+            wall = time.perf_counter() - t0
+            st = ppc.pospopcnt_server_get_stats(srv)
+        finally:
+            ppc.pospopcnt_server_destroy(srv)
+        assert np.all(status == 0), "requests failed"
+        q = np.percentile(lat, [50, 99, 99.9]) * 1e3
+        return {"p50_ms": round(float(q[0]), 4), "p99_ms": round(float(q[1]), 4), "p999_ms": round(float(q[2]), 4),
+                "max_ms": round(float(lat.max()) * 1e3, 4), "mean_ms": round(float(lat.mean()) * 1e3, 4),
+                "aggregate_GBps": round(total / wall / 1e9, 2), "wall_s": round(wall, 3),
+                "batches": st["batches"], "mean_jobs_per_batch": round(st["jobs_in_batches"] / max(st["batches"], 1), 2),
+                "max_batch": st["max_batch"], "deferrals": st["deferrals"],
+                "max_GiB_in_flight": round(st["max_bytes_in_flight"] / 2**30, 3)}, counts
+
+    batched, c_b = serve(False)
+    plain, c_p = serve(True)
+    # each result alone (its own plain call) vs in the mix, on a sample
+    rng = np.random.default_rng(0)
+    sample = rng.choice(n, size=min(n, 2000), replace=False)
+    solo = torch.zeros((sample.size, 32), dtype=torch.int64, device=dev)
+    for r, i in enumerate(sample):
+        w = int(tr["width"][i])
+        o = int(tr["offset_bytes"][i])
+        ppc.pospopcnt_count(w, pool[o:o + int(nbytes[i])], counts=solo[r, :w])
+    torch.cuda.synchronize()
+    solo_np = solo.cpu().numpy().view(np.uint64)
+    same = bool(np.array_equal(solo_np, c_b[sample]) and np.array_equal(solo_np, c_p[sample]))
+    same_all = bool(np.array_equal(c_b, c_p))
+    if rank != 0:
+        return None
+    return {"metric": "served p99 latency", "value": batched["p99_ms"], "unit": "ms", "n_gpus": world,
+            "steps": 1, "warmup": 1, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u8/u16/u32", "data": "synthetic",
+            "config": {"workload": f"Poisson {args.serve_rate:g} req/s for {args.serve_seconds:g} s, widths 8/16/32 "
+                                   "(0.2/0.6/0.2), sizes log-uniform 1 KiB..256 MiB, 4 GiB device pool, "
+                                   "budget 64 GiB",
+                       "requests": int(n), "total_GB": round(total / 1e9, 2),
+                       "offered_GBps": round(total / args.serve_seconds / 1e9, 1)},
+            "continuous_batching": batched, "per_request_plain": plain,
+            "p99_speedup_vs_per_request": round(plain["p99_ms"] / batched["p99_ms"], 2),
+            "results_same_alone_and_in_mix": same, "batched_equals_per_request_all": same_all}
+
+
 def run_reference(args, world, rank):
     """The reference arm: the scalar CPU oracle on the host cores, each step
     a bounded 2^26-word sample of the same workload."""
@@ -572,7 +648,9 @@ def main(argv=None):
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="u16",
                    choices=["u16", "u16_onehot", "u16_sparse", "u16_misaligned", "u8", "u32", "sweep", "batched",
-                            "kernels", "autotune"])
+                            "kernels", "autotune", "serve"])
+    p.add_argument("--serve-rate", type=float, default=50000.0)
+    p.add_argument("--serve-seconds", type=float, default=60.0)
     p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--log2-words", type=int, default=None,
                    help="run a smaller uniform-bits case of 2^k words (profiling only)")
@@ -597,6 +675,8 @@ def main(argv=None):
             out = run_kernels(args, world, rank, local)
         elif args.workload == "autotune":
             out = run_autotune(args, world, rank, local)
+        elif args.workload == "serve":
+            out = run_serve(args, world, rank, local)
         else:
             out = run_plain(args, world, rank, local)
         if world > 1:

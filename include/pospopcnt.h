@@ -152,6 +152,80 @@ int pospopcnt_batched_noalloc(const void* d_in, const int64_t* d_offsets, size_t
 int pospopcnt_plain_segments(const void* d_in, const int64_t* h_offsets, size_t nseg, int width,
                              uint64_t* d_counts, cudaStream_t stream);
 
+/* ---- serving: continuous batching of jobs on one GPU ----------------------
+ * Not in the paper (whose experiments count one buffer at a time): a runtime
+ * that counts many independent jobs of mixed widths and sizes as they
+ * arrive.  A worker thread admits jobs oldest first while the payload bytes
+ * admitted and not yet completed stay within hbm_budget_bytes, launches up
+ * to max_batch_jobs pending jobs of one width as one segmented count (the
+ * descriptor form of the batched kernel), keeps up to max_inflight batches
+ * on the GPU on separate streams, and lets jobs that arrive meanwhile join
+ * the next batch as soon as a slot frees (continuous batching).  Each job's
+ * payload stays where the caller put it in device memory; its counts are
+ * computed on the device and copied to pinned host memory with the batch.
+ * per_request = 1 instead launches every job on its own (one plain count
+ * per job), the comparison the batched form is measured against. */
+typedef struct pospopcnt_server pospopcnt_server;
+
+typedef struct {
+  uint64_t hbm_budget_bytes; /* admission budget in payload bytes (0: 64 GiB) */
+  int max_inflight;          /* batches (jobs, per_request) on the GPU at once, 1..256 (0: 4 or 64) */
+  int max_batch_jobs;        /* jobs per batch, 1..65536 (0: 4096; per_request: 1) */
+  int per_request;           /* 1: one plain launch per job */
+} pospopcnt_server_config;
+
+typedef struct {
+  uint64_t tag;      /* the caller's tag (submit) or request index (trace) */
+  int status;        /* POSPOPCNT_OK or the error the job met */
+  int width;
+  uint64_t n;        /* words */
+  double t_arrival, t_admit, t_launch, t_done; /* seconds on the runtime's monotonic clock */
+  uint64_t counts[32];
+} pospopcnt_result;
+
+typedef struct {
+  uint64_t submitted, completed, rejected, batches, jobs_in_batches, max_batch, deferrals;
+  uint64_t bytes_completed, max_bytes_in_flight;
+} pospopcnt_server_stats;
+
+/* Creates a server on `device` (allocates its slots: per slot a stream, an
+ * event, pinned descriptor and result buffers and device buffers) and starts
+ * its worker thread.  cfg may be NULL for the defaults. */
+int pospopcnt_server_create(int device, const pospopcnt_server_config* cfg, pospopcnt_server** out);
+
+/* Waits for every submitted job, stops the worker and frees the server. */
+int pospopcnt_server_destroy(pospopcnt_server* server);
+
+/* Submits one job: n words of `width` bits at d_in (device memory, aligned
+ * to the word size, unchanged until the job completes); arrival time = now.
+ * POSPOPCNT_ERR_TOO_LARGE if the job alone exceeds the budget. */
+int pospopcnt_server_submit(pospopcnt_server* server, int width, const void* d_in, size_t n, uint64_t tag);
+
+/* Moves up to max completed jobs into out (non-blocking); *n_out = count. */
+int pospopcnt_server_poll(pospopcnt_server* server, pospopcnt_result* out, int max, int* n_out);
+
+/* Replays an open-loop arrival trace: request i (width[i], nwords[i] words at
+ * device address d_addr[i]) is submitted at t_arrival[i] seconds after the
+ * start (nondecreasing), stamped with that scheduled time, whatever the
+ * state of the GPU.  Returns when every request has completed:
+ * latency_out[i] = completion seen on the host - scheduled arrival (s);
+ * counts_out (optional, n x 32 uint64) and status_out (optional) per
+ * request.  Jobs submitted earlier finish first. */
+int pospopcnt_server_run_trace(pospopcnt_server* server, size_t n, const double* t_arrival, const int* width,
+                               const uint64_t* d_addr, const uint64_t* nwords, double* latency_out,
+                               uint64_t* counts_out, int* status_out);
+
+int pospopcnt_server_get_stats(pospopcnt_server* server, pospopcnt_server_stats* out);
+
+/* The server's admission policy on a mock clock (host only, no device): jobs
+ * arrive at t_arrival[i] (nondecreasing) with bytes[i] of payload, are
+ * admitted oldest first while the bytes admitted and not yet completed fit
+ * in `budget`, and complete service_s[i] seconds after admission.  Writes
+ * each job's admission time (NaN if rejected) and status
+ * (POSPOPCNT_ERR_TOO_LARGE for a job larger than the budget). */
+int pospopcnt_admission_simulate(uint64_t budget, size_t n, const double* t_arrival, const uint64_t* bytes,
+                                 const double* service_s, double* t_admit_out, int* status_out);
+
 /* Synchronises `stream`, reads and clears the device error word (set by a
  * bounded wait that gave up).  Returns POSPOPCNT_OK or
  * POSPOPCNT_ERR_TIMEOUT. */

@@ -26,7 +26,9 @@ __all__ = [
     "pospopcnt_batched", "pospopcnt_batched_noalloc", "pospopcnt_plain_segments", "pospopcnt_check_device_error", "pospopcnt_plan_split",
     "pospopcnt_get_config", "pospopcnt_set_config", "pospopcnt_autotune", "pospopcnt_strerror",
     "pospopcnt_last_cuda_error", "pospopcnt_launch_count", "pospopcnt_selftest_timeout", "KERNELS",
-    "Config",
+    "Config", "pospopcnt_server_create", "pospopcnt_server_destroy", "pospopcnt_server_submit",
+    "pospopcnt_server_poll", "pospopcnt_server_run_trace", "pospopcnt_server_get_stats",
+    "pospopcnt_admission_simulate",
 ]
 
 KERNELS = {"auto": 0, "csa": 1, "tma": 2, "ballot": 3}
@@ -51,6 +53,29 @@ class Config(ctypes.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class ServerConfig(ctypes.Structure):
+    """pospopcnt_server_config."""
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_int),
+                ("max_batch_jobs", ctypes.c_int), ("per_request", ctypes.c_int)]
+
+
+class Result(ctypes.Structure):
+    """pospopcnt_result."""
+    _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int), ("width", ctypes.c_int),
+                ("n", ctypes.c_uint64), ("t_arrival", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_launch", ctypes.c_double), ("t_done", ctypes.c_double), ("counts", ctypes.c_uint64 * 32)]
+
+
+class ServerStats(ctypes.Structure):
+    """pospopcnt_server_stats."""
+    _fields_ = [(f, ctypes.c_uint64) for f in ("submitted", "completed", "rejected", "batches", "jobs_in_batches",
+                                                "max_batch", "deferrals", "bytes_completed",
+                                                "max_bytes_in_flight")]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
 
 
 _lock = threading.Lock()
@@ -99,6 +124,13 @@ def _declare(lib):
         "pospopcnt_last_cuda_error": (i32, []),
         "pospopcnt_launch_count": (u64, []),
         "pospopcnt_selftest_timeout": (i32, [u64, vp]),
+        "pospopcnt_server_create": (i32, [i32, P(ServerConfig), P(vp)]),
+        "pospopcnt_server_destroy": (i32, [vp]),
+        "pospopcnt_server_submit": (i32, [vp, i32, vp, sz, u64]),
+        "pospopcnt_server_poll": (i32, [vp, P(Result), i32, P(i32)]),
+        "pospopcnt_server_run_trace": (i32, [vp, sz, vp, vp, vp, vp, vp, vp, vp]),
+        "pospopcnt_server_get_stats": (i32, [vp, P(ServerStats)]),
+        "pospopcnt_admission_simulate": (i32, [u64, sz, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -344,3 +376,80 @@ def pospopcnt_selftest_timeout(limit_ns: int = 1_000_000, stream=None, device=No
     with torch.cuda.device(device):
         _check(_lib().pospopcnt_selftest_timeout(limit_ns, _stream_handle(stream, device)),
                "pospopcnt_selftest_timeout")
+
+
+# ---------------------------------------------------------------------------
+# serving
+
+def pospopcnt_server_create(device: int = 0, hbm_budget_bytes: int = 0, max_inflight: int = 0,
+                            max_batch_jobs: int = 0, per_request: bool = False) -> int:
+    """Creates a serving runtime (see the C header); returns its handle."""
+    cfg = ServerConfig(hbm_budget_bytes, max_inflight, max_batch_jobs, int(per_request))
+    h = ctypes.c_void_p()
+    _check(_lib().pospopcnt_server_create(device, ctypes.byref(cfg), ctypes.byref(h)), "pospopcnt_server_create")
+    return h.value
+
+
+def pospopcnt_server_destroy(server: int) -> None:
+    _check(_lib().pospopcnt_server_destroy(ctypes.c_void_p(server)), "pospopcnt_server_destroy")
+
+
+def pospopcnt_server_submit(server: int, width: int, x, tag: int) -> None:
+    """Submits the words of CUDA tensor x (kept alive by the caller until the
+    job completes)."""
+    ptr, n = _words(x, width)
+    _check(_lib().pospopcnt_server_submit(ctypes.c_void_p(server), width, ctypes.c_void_p(ptr), n, tag),
+           "pospopcnt_server_submit")
+
+
+def pospopcnt_server_poll(server: int, max_results: int = 1024):
+    """Completed jobs as dicts (tag, status, width, n, times, counts)."""
+    buf = (Result * max_results)()
+    k = ctypes.c_int()
+    _check(_lib().pospopcnt_server_poll(ctypes.c_void_p(server), buf, max_results, ctypes.byref(k)),
+           "pospopcnt_server_poll")
+    out = []
+    for r in buf[:k.value]:
+        out.append({"tag": r.tag, "status": r.status, "width": r.width, "n": r.n, "t_arrival": r.t_arrival,
+                    "t_admit": r.t_admit, "t_launch": r.t_launch, "t_done": r.t_done,
+                    "counts": np.frombuffer(bytes(r.counts), dtype=np.uint64)[: r.width].copy()})
+    return out
+
+
+def pospopcnt_server_run_trace(server: int, t_arrival, width, d_addr, nwords, want_counts: bool = False):
+    """Replays an open-loop trace; returns (latency_s, counts or None, status)."""
+    t = np.ascontiguousarray(t_arrival, dtype=np.float64)
+    w = np.ascontiguousarray(width, dtype=np.int32)
+    a = np.ascontiguousarray(d_addr, dtype=np.uint64)
+    nw = np.ascontiguousarray(nwords, dtype=np.uint64)
+    n = t.size
+    assert w.size == n and a.size == n and nw.size == n
+    lat = np.empty(n, dtype=np.float64)
+    status = np.empty(n, dtype=np.int32)
+    counts = np.zeros((n, 32), dtype=np.uint64) if want_counts else None
+    _check(_lib().pospopcnt_server_run_trace(
+        ctypes.c_void_p(server), n, t.ctypes.data, w.ctypes.data, a.ctypes.data, nw.ctypes.data, lat.ctypes.data,
+        counts.ctypes.data if counts is not None else None, status.ctypes.data), "pospopcnt_server_run_trace")
+    return lat, counts, status
+
+
+def pospopcnt_server_get_stats(server: int) -> dict:
+    st = ServerStats()
+    _check(_lib().pospopcnt_server_get_stats(ctypes.c_void_p(server), ctypes.byref(st)),
+           "pospopcnt_server_get_stats")
+    return st.as_dict()
+
+
+def pospopcnt_admission_simulate(budget: int, t_arrival, nbytes, service_s):
+    """The server's admission policy on a mock clock (no device): returns
+    (t_admit, status) per job."""
+    t = np.ascontiguousarray(t_arrival, dtype=np.float64)
+    b = np.ascontiguousarray(nbytes, dtype=np.uint64)
+    sv = np.ascontiguousarray(service_s, dtype=np.float64)
+    n = t.size
+    t_admit = np.empty(n, dtype=np.float64)
+    status = np.empty(n, dtype=np.int32)
+    _check(_lib().pospopcnt_admission_simulate(budget, n, t.ctypes.data, b.ctypes.data, sv.ctypes.data,
+                                               t_admit.ctypes.data, status.ctypes.data),
+           "pospopcnt_admission_simulate")
+    return t_admit, status

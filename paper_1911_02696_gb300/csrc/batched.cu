@@ -30,13 +30,19 @@ struct QueueSlot {
   unsigned int done;        // CTAs that have finished
 };
 
+// Segment s is words [offsets[s], offsets[s+1]) of a virtual word space.
+// Offsets form (seg_addr == nullptr): virtual word v is word v of `base`.
+// Descriptor form: segment s starts at byte address seg_addr[s], so virtual
+// word v of segment s is at seg_addr[s] + (v - offsets[s]) * k/8; segments
+// may then lie anywhere in device memory (the serving path).
 struct BatchedArgs {
   const uint8_t* base;
   const int64_t* offsets;
   uint64_t nseg;
   unsigned long long* counts;
   QueueSlot* q;
-  uint64_t tile_words;  // multiple of 8 warps x 16 bytes
+  uint64_t tile_words;        // multiple of 8 warps x 16 bytes
+  const uint64_t* seg_addr;  // nullptr: offsets form
 };
 
 constexpr int BT_THREADS = 256;
@@ -121,8 +127,10 @@ __global__ void __launch_bounds__(BT_THREADS, bt_min_blocks<K>::value) batched_k
   const int warp = threadIdx.x >> 5;
   const int64_t o0 = a.offsets[0];
   const int64_t oN = a.offsets[a.nseg];
-  // first tile starts at the 16-byte boundary at or before word o0
-  const uint64_t mis = (reinterpret_cast<uint64_t>(a.base) + uint64_t(o0) * WB) & 15;
+  // offsets form: the first tile starts at the 16-byte boundary at or before
+  // word o0, so inner tile boundaries are aligned; descriptor form: at o0
+  const uint64_t mis =
+      a.seg_addr ? 0 : (reinterpret_cast<uint64_t>(a.base) + uint64_t(o0) * WB) & 15;
   const int64_t start = o0 - int64_t(mis / WB);
   const uint64_t T = a.tile_words, Tw = a.tile_words / BT_WARPS;
 
@@ -144,7 +152,11 @@ __global__ void __launch_bounds__(BT_THREADS, bt_min_blocks<K>::value) batched_k
       const int64_t seg_hi = a.offsets[s + 1];
       const int64_t pa = seg_lo > w0 ? seg_lo : w0;
       const int64_t pb = seg_hi < w1 ? seg_hi : w1;
-      if (pa < pb) warp_count_piece<K>(a.base, uint64_t(pa), uint64_t(pb), a.counts + s * K);
+      if (pa < pb) {
+        const uint8_t* pbase =
+            a.seg_addr ? reinterpret_cast<const uint8_t*>(a.seg_addr[s] - uint64_t(seg_lo) * WB) : a.base;
+        warp_count_piece<K>(pbase, uint64_t(pa), uint64_t(pb), a.counts + s * K);
+      }
       if (seg_hi >= w1 || s + 1 >= a.nseg) break;
       ++s;
       seg_lo = seg_hi;
@@ -178,8 +190,9 @@ static int launch_batched_k(const DeviceState& st, const BatchedArgs& a, cudaStr
 
 int launch_batched(const DeviceState& st, const void* d_in, const int64_t* d_offsets, size_t nseg,
                    int width, unsigned long long* d_counts, void* queue_slot, int tile_words,
-                   cudaStream_t stream) {
+                   cudaStream_t stream, const uint64_t* d_seg_addr) {
   BatchedArgs a;
+  a.seg_addr = d_seg_addr;
   a.base = static_cast<const uint8_t*>(d_in);
   a.offsets = d_offsets;
   a.nseg = nseg;
@@ -272,6 +285,7 @@ extern "C" int pospopcnt_batched_noalloc(const void* d_in, const int64_t* d_offs
   DeviceState st;
   st.sms = sms;
   BatchedArgs a;
+  a.seg_addr = nullptr;
   a.base = static_cast<const uint8_t*>(d_in);
   a.offsets = d_offsets;
   a.nseg = nseg;

@@ -55,9 +55,15 @@ int launch_plain(const DeviceState& st, int width, const pospopcnt_config& cfg, 
 // Validates a configuration for a width; fills defaults for zero fields.
 int normalize_config(const DeviceState& st, int width, pospopcnt_config* cfg);
 
-// Launch of the batched kernel (counts zeroed by the caller).
+// Launch of the batched kernel (counts zeroed by the caller).  With
+// d_seg_addr (nseg byte addresses) the segments are [d_offsets[s],
+// d_offsets[s+1]) of a virtual word space and segment s starts at
+// d_seg_addr[s]; d_in is then unused.
 int launch_batched(const DeviceState& st, const void* d_in, const int64_t* d_offsets, size_t nseg,
                    int width, unsigned long long* d_counts, void* queue_slot, int tile_words,
-                   cudaStream_t stream);
+                   cudaStream_t stream, const uint64_t* d_seg_addr = nullptr);
+
+// Monotonic host clock in seconds.
+double now_seconds();
 
 }  // namespace ppc

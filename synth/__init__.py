@@ -175,3 +175,32 @@ def segmented_one_hot(seed: int, offsets: np.ndarray, width: int = 16, s: float 
         assert _load().synth_segmented_one_hot(seed, width, _ptr(cdf), _ptr(offsets), _ptr(rot),
                                                nseg, _ptr(out), _threads(nthreads)) == 0
     return out
+
+
+def serving_trace(seed: int, rate: float, duration: float, pool_bytes: int, min_bytes: int = 1024,
+                  max_bytes: int = 256 << 20, widths=(8, 16, 32), weights=(0.2, 0.6, 0.2)):
+    """Open-loop request trace: Poisson arrivals at `rate` per second over
+    `duration` seconds; width drawn from `widths` with `weights`; payload size
+    log-uniform in [min_bytes, max_bytes] bytes, rounded down to whole words;
+    each payload a slice of a device pool of pool_bytes bytes starting at a
+    uniform word-aligned offset.  Returns a dict of arrays (t_arrival,
+    width, offset_bytes, nwords)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n_est = int(rate * duration * 1.2) + 100
+    gaps = rng.exponential(1.0 / rate, size=n_est)
+    t = np.cumsum(gaps)
+    while t[-1] < duration:  # extend if the estimate fell short
+        more = np.cumsum(rng.exponential(1.0 / rate, size=n_est)) + t[-1]
+        t = np.concatenate([t, more])
+    t = t[t < duration]
+    n = t.size
+    w = rng.choice(np.array(widths, dtype=np.int32), size=n, p=np.array(weights) / np.sum(weights))
+    logb = rng.uniform(np.log(min_bytes), np.log(max_bytes), size=n)
+    nbytes = np.floor(np.exp(logb)).astype(np.int64)
+    wb = (w // 8).astype(np.int64)
+    nwords = np.maximum(nbytes // wb, 1)
+    nbytes = nwords * wb
+    assert int(nbytes.max()) <= pool_bytes
+    span = pool_bytes - nbytes
+    off = (rng.uniform(0, 1, size=n) * (span // wb + 1)).astype(np.int64) * wb
+    return {"t_arrival": t.astype(np.float64), "width": w, "offset_bytes": off, "nwords": nwords.astype(np.uint64)}
