@@ -558,8 +558,9 @@ def run_serve(args, world, rank, local):
 
     def serve(per_request):
         srv = ppc.pospopcnt_server_create(local, hbm_budget_bytes=64 << 30, per_request=per_request,
-                                          max_inflight=64 if per_request else 4,
-                                          max_batch_jobs=1 if per_request else 4096)
+                                          max_inflight=args.serve_slots_plain if per_request else args.serve_slots,
+                                          max_batch_jobs=1 if per_request else 240,
+                                          large_job_bytes=int(args.serve_large_mib * (1 << 20)))
         try:
             # warm-up: a short slice of the trace
             k = min(n, 2000)
@@ -604,7 +605,9 @@ def run_serve(args, world, rank, local):
                                    "(0.2/0.6/0.2), sizes log-uniform 1 KiB..256 MiB, 4 GiB device pool, "
                                    "budget 64 GiB",
                        "requests": int(n), "total_GB": round(total / 1e9, 2),
-                       "offered_GBps": round(total / args.serve_seconds / 1e9, 1)},
+                       "offered_GBps": round(total / args.serve_seconds / 1e9, 1),
+                       "batched_slots": args.serve_slots, "per_request_slots": args.serve_slots_plain,
+                       "large_job_MiB": args.serve_large_mib},
             "continuous_batching": batched, "per_request_plain": plain,
             "p99_speedup_vs_per_request": round(plain["p99_ms"] / batched["p99_ms"], 2),
             "results_same_alone_and_in_mix": same, "batched_equals_per_request_all": same_all}
@@ -651,6 +654,10 @@ def main(argv=None):
                             "kernels", "autotune", "serve"])
     p.add_argument("--serve-rate", type=float, default=50000.0)
     p.add_argument("--serve-seconds", type=float, default=60.0)
+    p.add_argument("--serve-slots", type=int, default=16, help="batches in flight (continuous batching)")
+    p.add_argument("--serve-slots-plain", type=int, default=64, help="requests in flight (per-request mode)")
+    p.add_argument("--serve-large-mib", type=float, default=4.0,
+                   help="jobs at least this large are launched on their own")
     p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--log2-words", type=int, default=None,
                    help="run a smaller uniform-bits case of 2^k words (profiling only)")

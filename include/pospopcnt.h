@@ -158,20 +158,25 @@ int pospopcnt_plain_segments(const void* d_in, const int64_t* h_offsets, size_t 
  * arrive.  A worker thread admits jobs oldest first while the payload bytes
  * admitted and not yet completed stay within hbm_budget_bytes, launches up
  * to max_batch_jobs pending jobs of one width as one segmented count (the
- * descriptor form of the batched kernel), keeps up to max_inflight batches
- * on the GPU on separate streams, and lets jobs that arrive meanwhile join
- * the next batch as soon as a slot frees (continuous batching).  Each job's
- * payload stays where the caller put it in device memory; its counts are
- * computed on the device and copied to pinned host memory with the batch.
- * per_request = 1 instead launches every job on its own (one plain count
- * per job), the comparison the batched form is measured against. */
+ * job table travels in the kernel's parameters), keeps up to max_inflight
+ * batches on the GPU on separate streams, and lets jobs that arrive
+ * meanwhile join the next batch as soon as a slot frees (continuous
+ * batching).  Each job's payload stays where the caller put it in device
+ * memory; the GPU writes each job's counts to pinned host memory and flags
+ * that job complete as soon as its own last piece is counted, so a job never
+ * waits for the rest of its batch.
+ * Jobs of at least large_job_bytes are launched on their own with the
+ * tuned plain count.  per_request = 1 launches every job that way (one
+ * plain count per job), the comparison the batched form is measured
+ * against. */
 typedef struct pospopcnt_server pospopcnt_server;
 
 typedef struct {
   uint64_t hbm_budget_bytes; /* admission budget in payload bytes (0: 64 GiB) */
-  int max_inflight;          /* batches (jobs, per_request) on the GPU at once, 1..256 (0: 4 or 64) */
-  int max_batch_jobs;        /* jobs per batch, 1..65536 (0: 4096; per_request: 1) */
+  int max_inflight;          /* batches (jobs, per_request) on the GPU at once, 1..256 (0: 16 or 64) */
+  int max_batch_jobs;        /* jobs per batch, 1..240 (0: 240; per_request: 1) */
   int per_request;           /* 1: one plain launch per job */
+  uint64_t large_job_bytes;  /* jobs at least this large get their own plain launch (0: 4 MiB) */
 } pospopcnt_server_config;
 
 typedef struct {

@@ -22,13 +22,9 @@
 
 #include "device_common.cuh"
 #include "internal.h"
+#include "segment_common.cuh"
 
 namespace ppc {
-
-struct QueueSlot {
-  unsigned long long next;  // next tile index to hand out
-  unsigned int done;        // CTAs that have finished
-};
 
 // Segment s is words [offsets[s], offsets[s+1]) of a virtual word space.
 // Offsets form (seg_addr == nullptr): virtual word v is word v of `base`.
@@ -45,85 +41,21 @@ struct BatchedArgs {
   const uint64_t* seg_addr;  // nullptr: offsets form
 };
 
-constexpr int BT_THREADS = 256;
-constexpr int BT_WARPS = BT_THREADS / 32;
-// resident CTAs per SM the kernel is compiled for (register cap 65536 / (256 x this))
-template <int K>
-struct bt_min_blocks {
-  static constexpr int value = K == 32 ? 3 : 5;
-};
-
-// Largest s in [0, nseg) with offsets[s] <= w (requires offsets[0] <= w <
-// offsets[nseg]).  Each round the 32 lanes probe 32 evenly spaced candidates.
-__device__ __forceinline__ uint64_t find_segment(const int64_t* offsets, uint64_t nseg, int64_t w) {
-  const int lane = threadIdx.x & 31;
-  uint64_t lo = 0, hi = nseg - 1;  // answer in [lo, hi]
-  while (hi > lo) {
-    const uint64_t span = hi - lo + 1;
-    const uint64_t step = (span + 31) / 32;
-    const uint64_t idx = lo + uint64_t(lane) * step;
-    const bool le = idx <= hi && offsets[idx] <= w;
-    const unsigned m = __ballot_sync(FULL_MASK, le);  // lane 0 always true
-    const int j = 31 - __clz(m);
-    lo = lo + uint64_t(j) * step;
-    const uint64_t nhi = lo + step - 1;
-    hi = nhi < hi ? nhi : hi;
-    if (step == 1) break;
-  }
-  return lo;
-}
 
 // Counts words [pa, pb) of `base` with the whole warp and adds the result to
 // row[0..K-1].
 template <int K>
 __device__ __forceinline__ void warp_count_piece(const uint8_t* base, uint64_t pa, uint64_t pb,
                                                  unsigned long long* row) {
-  constexpr int WB = K / 8;
   constexpr int SH = 5 - ilog2<K>::value;
   const int lane = threadIdx.x & 31;
-  const uint64_t A = reinterpret_cast<uint64_t>(base) + pa * WB;
-  const uint64_t E = reinterpret_cast<uint64_t>(base) + pb * WB;
-  uint64_t bodyA = (A + 15) & ~uint64_t(15);
-  if (bodyA > E) bodyA = E;
-  uint64_t bodyE = E & ~uint64_t(15);
-  if (bodyE < bodyA) bodyE = bodyA;
-  const uint64_t nvec = (bodyE - bodyA) / 16;
-  // lanes 0..14 take the head words, lanes 16..30 the tail words (<= 15 each);
-  // loaded before the body loop so only this word stays live across it
-  const uint32_t head_words = uint32_t((bodyA - A) / WB);
-  const uint32_t tail_words = uint32_t((E - bodyE) / WB);
-  uint32_t edge = 0;
-  if (uint32_t(lane) < head_words)
-    edge = load_word<K>(reinterpret_cast<const uint8_t*>(A) + lane * WB);
-  else if (lane >= 16 && uint32_t(lane - 16) < tail_words)
-    edge = load_word<K>(reinterpret_cast<const uint8_t*>(bodyE) + (lane - 16) * WB);
-
-  uint32_t B[4] = {0, 0, 0, 0};
-  uint32_t top[K];
-#pragma unroll
-  for (int p = 0; p < K; ++p) top[p] = 0;
-  const uint4* vp = reinterpret_cast<const uint4*>(bodyA);
-  for (uint64_t bv = 0; bv < nvec; bv += 128) {  // 32 lanes x 4 vectors per trip
-    uint32_t d[16];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const uint64_t idx = bv + uint64_t(j) * 32 + lane;
-      const uint4 x = idx < nvec ? ld_stream(vp + idx) : make_uint4(0, 0, 0, 0);
-      d[4 * j + 0] = x.x, d[4 * j + 1] = x.y, d[4 * j + 2] = x.z, d[4 * j + 3] = x.w;
-    }
-    flush<K>(top, Circuit<4>::run(d, B));
-  }
-  uint32_t c[K];
-  finalize<K, 4>(c, top, B);
-  count_word<K>(c, edge);
-  const uint32_t v = warp_reduce_positions<K>(c);
+  const uint32_t v = warp_piece_counts<K>(base, pa, pb);
   if ((lane & ((1 << SH) - 1)) == 0 && v) atomicAdd(row + (lane >> SH), (unsigned long long)v);
 }
 
 template <int K>
 __global__ void __launch_bounds__(BT_THREADS, bt_min_blocks<K>::value) batched_kernel(BatchedArgs a) {
   constexpr int WB = K / 8;
-  __shared__ unsigned long long s_tile;
   const int warp = threadIdx.x >> 5;
   const int64_t o0 = a.offsets[0];
   const int64_t oN = a.offsets[a.nseg];
@@ -135,10 +67,7 @@ __global__ void __launch_bounds__(BT_THREADS, bt_min_blocks<K>::value) batched_k
   const uint64_t T = a.tile_words, Tw = a.tile_words / BT_WARPS;
 
   for (;;) {
-    if (threadIdx.x == 0) s_tile = atomicAdd(&a.q->next, 1ull);
-    __syncthreads();
-    const uint64_t tile = s_tile;
-    __syncthreads();
+    const uint64_t tile = pop_tile(a.q);
     if (oN <= start || tile >= (uint64_t(oN - start) + T - 1) / T) break;
     const int64_t t0 = start + int64_t(tile * T);
     int64_t w0 = t0 + int64_t(warp * Tw);
@@ -162,17 +91,7 @@ __global__ void __launch_bounds__(BT_THREADS, bt_min_blocks<K>::value) batched_k
       seg_lo = seg_hi;
     }
   }
-  // the last CTA out resets the queue slot for the next launch
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned prev = atomicAdd(&a.q->done, 1u);
-    if (prev == gridDim.x - 1) {
-      atomicExch(&a.q->next, 0ull);
-      atomicExch(&a.q->done, 0u);
-      __threadfence();
-    }
-  }
+  retire_cta(a.q);
 }
 
 template <int K>

@@ -2,22 +2,37 @@
 //
 // Jobs (width, device pointer, word count) arrive from clients at any time.
 // A worker thread owns the GPU side:
-//   1. completion: polls the event of every batch in flight; when one has
-//      finished, copies each job's counts (already on the host, pinned) to
-//      its sink, stamps the completion time and releases the job's bytes
-//      from the HBM budget;
+//   1. completion: reads, for every job in flight, a flag in pinned host
+//      memory that the GPU sets when that job's counts are final (a job
+//      finishes on its own, not with its batch); a finished job's counts are
+//      already on the host; its bytes are released from the HBM budget;
 //   2. admission: moves arrived jobs, oldest first, from the waiting queue
 //      to the pending queue of their width while the payload bytes admitted
 //      and not yet completed stay within the budget (AdmissionPolicy);
-//   3. launch: while a slot (stream + pinned descriptor and result buffers +
-//      device buffers) is free, takes up to max_batch_jobs pending jobs of
-//      the width whose oldest job arrived first and launches them as one
-//      segmented count (descriptor form of the batched kernel), followed by
-//      the copy of their counts to the host and an event.
+//   3. launch: while a slot (stream + device rows + pinned result area) is
+//      free, takes up to max_batch_jobs (<= 240) pending jobs of the width
+//      whose oldest job arrived first and launches them as one segmented
+//      count.  The job table travels in the kernel's parameters; the grid
+//      has one CTA per tile of the batch.
 // Several batches run on the GPU at once, and jobs that arrive while others
 // are on the GPU join the next batch as soon as a slot and budget free up:
 // batching is continuous, not a queue drained one batch at a time.
-// In per-request mode every job is its own plain count launch (the
+//
+// Device side (serve_kernel): one CTA per 64 KiB tile of the batch's
+// virtual word space (short-lived CTAs, so batches on other streams share
+// the SMs at fine grain); each warp counts the pieces of its sub-range (segment helpers shared with the batched kernel) and adds them
+// into the job's row in device memory.  Every warp then bumps the job's
+// piece counter; the warp that completes it (the number of sub-ranges a job
+// overlaps is known from its bounds) reads and re-zeroes the row, writes the
+// counts to the job's pinned host slot, fences at system scope and stores
+// the batch ticket into the job's flag.  Rows and counters are left zero for
+// the slot's next batch, so no memset or device-to-host copy is issued.
+//
+// Jobs of at least large_job_bytes (default 4 MiB) gain nothing from
+// batching -- their transfer time dwarfs a launch -- and would make every
+// warp of a batch add into one row; each is launched on its own slot with
+// the tuned plain count (block-level reduction), followed by a copy of its
+// counts and an event.  In per-request mode every job takes that route (the
 // comparison the batched form is measured against).
 #include <cuda_runtime.h>
 
@@ -33,6 +48,7 @@
 
 #include "internal.h"
 #include "pospopcnt.h"
+#include "segment_common.cuh"
 
 namespace ppc {
 
@@ -52,6 +68,78 @@ struct AdmissionPolicy {
   void release(uint64_t bytes) { in_flight -= bytes; }
 };
 
+constexpr int SERVE_MAX_JOBS = 240;  // job table in the kernel parameters (< 4 KiB)
+constexpr uint64_t SERVE_TILE_BYTES = 64 * 1024;  // one CTA: 8 warps x 8 KiB
+
+struct ServeArgs {
+  int64_t bounds[SERVE_MAX_JOBS + 1];  // virtual word offsets: job s is [bounds[s], bounds[s+1])
+  uint64_t addr[SERVE_MAX_JOBS];       // byte address of each job's first word
+  uint32_t nseg;
+  uint32_t ticket;                     // stored into a job's flag when its counts are final
+  uint64_t tile_words;                 // multiple of 8 warps x 16 bytes
+  unsigned long long* rows;            // device, SERVE_MAX_JOBS x 32, zero on entry and exit
+  unsigned* pieces;                    // device, SERVE_MAX_JOBS, zero on entry and exit
+  unsigned long long* h_counts;        // device view of pinned host memory, SERVE_MAX_JOBS x 32
+  unsigned* h_flags;                   // device view of pinned host memory, SERVE_MAX_JOBS
+};
+
+template <int K>
+__global__ void __launch_bounds__(BT_THREADS, bt_min_blocks<K>::value) serve_kernel(const __grid_constant__ ServeArgs a) {
+  constexpr int WB = K / 8;
+  constexpr int SH = 5 - ilog2<K>::value;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t oN = a.bounds[a.nseg];  // bounds[0] == 0
+  const uint64_t T = a.tile_words, Tw = a.tile_words / BT_WARPS;
+  // one CTA per tile (no persistent loop): CTAs live a few microseconds, so
+  // the kernels of other batches get SM slots without waiting for this one
+  {
+    const uint64_t tile = blockIdx.x;
+    int64_t w0 = int64_t(tile * T + warp * Tw);
+    int64_t w1 = w0 + int64_t(Tw);
+    if (w1 > oN) w1 = oN;
+    if (w0 >= w1) return;
+    uint64_t s = find_segment(a.bounds, a.nseg, w0);
+    int64_t seg_lo = a.bounds[s];
+    for (;;) {
+      const int64_t seg_hi = a.bounds[s + 1];
+      const int64_t pa = seg_lo > w0 ? seg_lo : w0;
+      const int64_t pb = seg_hi < w1 ? seg_hi : w1;
+      if (pa < pb) {
+        const uint8_t* pbase = reinterpret_cast<const uint8_t*>(a.addr[s] - uint64_t(seg_lo) * WB);
+        const uint32_t v = warp_piece_counts<K>(pbase, uint64_t(pa), uint64_t(pb));
+        unsigned long long* row = a.rows + s * 32;
+        if ((lane & ((1 << SH) - 1)) == 0 && v) atomicAdd(row + (lane >> SH), (unsigned long long)v);
+        // the warp that adds the job's last piece publishes its counts
+        const unsigned expected = unsigned((uint64_t(seg_hi) - 1) / Tw - uint64_t(seg_lo) / Tw + 1);
+        __syncwarp();
+        unsigned last = 0;
+        if (lane == 0) {
+          __threadfence();
+          last = atomicAdd(a.pieces + s, 1u) + 1u == expected ? 1u : 0u;
+        }
+        last = __shfl_sync(FULL_MASK, last, 0);
+        if (last) {
+          __threadfence();
+          const unsigned long long c = lane < K ? atomicExch(row + lane, 0ull) : 0ull;
+#pragma unroll
+          for (int p = 0; p < K; ++p) {
+            const unsigned long long cp = __shfl_sync(FULL_MASK, c, p);
+            if (lane == 0) a.h_counts[s * 32 + p] = cp;
+          }
+          if (lane == 0) {
+            a.pieces[s] = 0;
+            __threadfence_system();
+            *reinterpret_cast<volatile unsigned*>(a.h_flags + s) = a.ticket;
+          }
+        }
+      }
+      if (seg_hi >= w1 || s + 1 >= a.nseg) break;
+      ++s;
+      seg_lo = seg_hi;
+    }
+  }
+}
+
 namespace {
 
 struct Job {
@@ -68,15 +156,23 @@ int widx(int w) { return w == 8 ? 0 : w == 16 ? 1 : 2; }
 
 struct Slot {
   cudaStream_t stream = nullptr;
-  cudaEvent_t done = nullptr;
-  uint64_t* h_desc = nullptr;               // pinned: bounds[m+1] then addr[m]
-  unsigned long long* h_results = nullptr;  // pinned: m x width
-  uint64_t* d_desc = nullptr;
-  unsigned long long* d_results = nullptr;
-  void* d_queue = nullptr;
+  cudaEvent_t done = nullptr;               // after the kernel (watchdog; per-request completion)
+  unsigned long long* d_rows = nullptr;     // device SERVE_MAX_JOBS x 32, zero between batches
+  unsigned* d_pieces = nullptr;             // device SERVE_MAX_JOBS
+  unsigned long long* d_single = nullptr;   // device, 32: a single job's counts (rows stay zero)
+  unsigned long long* h_single = nullptr;   // pinned: its copy on the host
+  unsigned long long* h_counts = nullptr;   // pinned, mapped: SERVE_MAX_JOBS x 32
+  unsigned* h_flags = nullptr;              // pinned, mapped: SERVE_MAX_JOBS
+  unsigned long long* dv_counts = nullptr;  // device views of h_counts / h_flags
+  unsigned* dv_flags = nullptr;
+  uint32_t ticket = 0;
   std::vector<Job> jobs;
+  std::vector<char> finished;
+  size_t remaining = 0;
+  double t_launch = 0;
   int width = 16;
   bool busy = false;
+  bool single = false;  // one job counted by a plain launch; completion by event
 };
 
 }  // namespace
@@ -87,11 +183,14 @@ struct Server {
   DeviceState* st = nullptr;
   std::vector<Slot> slots;
   void* d_pool = nullptr;  // one allocation for every slot's device buffers
+  void* h_pool = nullptr;  // one pinned, mapped allocation for every slot's host results
 
   std::mutex in_mu;
   std::deque<Job> incoming;
   std::deque<Job> waiting;
-  std::deque<Job> pending[3];
+  std::deque<Job> pending[3];   // small jobs, per width: batched
+  std::deque<Job> pending_large;  // jobs of >= large_job_bytes: one plain launch each
+  uint64_t large_job_bytes = 0;
   AdmissionPolicy adm;
   uint64_t admitted_jobs = 0;
 
@@ -137,31 +236,54 @@ struct Server {
     total_completed.fetch_add(1, std::memory_order_release);
   }
 
+  void finish(Slot& s, size_t i, const unsigned long long* counts, int status, double t) {
+    Job& j = s.jobs[i];
+    j.t_done = t;
+    adm.release(j.bytes);
+    emit(j, counts, status);
+    s.finished[i] = 1;
+    --s.remaining;
+    --admitted_jobs;
+    std::lock_guard<std::mutex> lk(stats_mu);
+    ++stats.completed;
+    stats.bytes_completed += j.bytes;
+  }
+
   bool poll_completions() {
     bool any = false;
     for (Slot& s : slots) {
       if (!s.busy) continue;
-      const cudaError_t q = cudaEventQuery(s.done);
-      if (q == cudaErrorNotReady) continue;
-      const double t = now_seconds();
-      const int status = q == cudaSuccess ? POSPOPCNT_OK : cuda_fail(q);
-      uint64_t bytes = 0;
-      for (size_t i = 0; i < s.jobs.size(); ++i) {
-        Job& j = s.jobs[i];
-        j.t_done = t;
-        adm.release(j.bytes);
-        bytes += j.bytes;
-        emit(j, s.h_results + i * size_t(s.width), status);
+      if (s.single) {
+        const cudaError_t q = cudaEventQuery(s.done);
+        if (q == cudaErrorNotReady) continue;
+        finish(s, 0, s.h_single, q == cudaSuccess ? POSPOPCNT_OK : cuda_fail(q), now_seconds());
+      } else {
+        for (size_t i = 0; i < s.jobs.size(); ++i) {
+          if (s.finished[i]) continue;
+          if (__atomic_load_n(s.h_flags + i, __ATOMIC_ACQUIRE) != s.ticket) continue;
+          finish(s, i, s.h_counts + i * 32, POSPOPCNT_OK, now_seconds());
+          any = true;
+        }
+        // watchdog: the kernel ended (or failed) without publishing every job
+        if (s.remaining && now_seconds() - s.t_launch > 0.5) {
+          const cudaError_t q = cudaEventQuery(s.done);
+          if (q != cudaErrorNotReady) {
+            const double t = now_seconds();
+            for (size_t i = 0; i < s.jobs.size(); ++i) {
+              if (s.finished[i]) continue;
+              if (__atomic_load_n(s.h_flags + i, __ATOMIC_ACQUIRE) == s.ticket)
+                finish(s, i, s.h_counts + i * 32, POSPOPCNT_OK, t);
+              else
+                finish(s, i, nullptr, q == cudaSuccess ? POSPOPCNT_ERR_CUDA : cuda_fail(q), t);
+            }
+          }
+        }
       }
-      admitted_jobs -= s.jobs.size();
-      {
-        std::lock_guard<std::mutex> lk(stats_mu);
-        stats.completed += s.jobs.size();
-        stats.bytes_completed += bytes;
+      if (s.remaining == 0) {
+        s.jobs.clear();
+        s.busy = false;
+        any = true;
       }
-      s.jobs.clear();
-      s.busy = false;
-      any = true;
     }
     return any;
   }
@@ -175,7 +297,7 @@ struct Server {
       }
     }
     bool any = false;
-    const uint64_t max_admitted = uint64_t(slots.size()) * uint64_t(cfg.max_batch_jobs) * 2;
+    const uint64_t max_admitted = uint64_t(slots.size()) * uint64_t(cfg.max_batch_jobs) * 4;
     while (!waiting.empty()) {
       Job& j = waiting.front();
       if (!adm.fits(j.bytes) || admitted_jobs >= max_admitted) {
@@ -189,7 +311,10 @@ struct Server {
       adm.admit(j.bytes);
       ++admitted_jobs;
       j.t_admit = now_seconds();
-      pending[widx(j.width)].push_back(j);
+      if (cfg.per_request || j.bytes >= large_job_bytes)
+        pending_large.push_back(j);
+      else
+        pending[widx(j.width)].push_back(j);
       waiting.pop_front();
       any = true;
     }
@@ -200,79 +325,103 @@ struct Server {
     return any;
   }
 
-  // width index whose oldest pending job arrived first, or -1
-  int oldest_width() const {
+  // the queue whose oldest job arrived first: 0..2 = small jobs of width
+  // 8/16/32, 3 = large jobs; -1 if nothing is pending
+  int oldest_queue() const {
     int best = -1;
+    double t = 0;
     for (int w = 0; w < 3; ++w)
-      if (!pending[w].empty() && (best < 0 || pending[w].front().t_arrival < pending[best].front().t_arrival))
-        best = w;
+      if (!pending[w].empty() && (best < 0 || pending[w].front().t_arrival < t)) best = w, t = pending[w].front().t_arrival;
+    if (!pending_large.empty() && (best < 0 || pending_large.front().t_arrival < t)) best = 3;
     return best;
   }
 
-  int launch(Slot& s, int wi) {
+  template <int K>
+  cudaError_t launch_serve(Slot& s, const ServeArgs& args, uint64_t total_words) {
+    const uint64_t tiles = (total_words + args.tile_words - 1) / args.tile_words;
+    serve_kernel<K><<<unsigned(std::max<uint64_t>(1, tiles)), BT_THREADS, 0, s.stream>>>(args);
+    note_launch();
+    return cudaGetLastError();
+  }
+
+  int launch(Slot& s, int qi) {
     static const int widths[3] = {8, 16, 32};
-    const int width = widths[wi];
-    const size_t take = std::min<size_t>(pending[wi].size(), size_t(cfg.max_batch_jobs));
+    std::deque<Job>& src = qi == 3 ? pending_large : pending[qi];
+    const size_t take = qi == 3 ? 1 : std::min<size_t>(src.size(), size_t(cfg.max_batch_jobs));
+    s.single = qi == 3;
+    const int width = s.single ? src.front().width : widths[qi];
     s.width = width;
-    s.jobs.assign(pending[wi].begin(), pending[wi].begin() + long(take));
-    pending[wi].erase(pending[wi].begin(), pending[wi].begin() + long(take));
-    const double t = now_seconds();
-    for (Job& j : s.jobs) j.t_launch = t;
+    s.jobs.assign(src.begin(), src.begin() + long(take));
+    src.erase(src.begin(), src.begin() + long(take));
     const size_t m = s.jobs.size();
-    cudaError_t e;
+    s.finished.assign(m, 0);
+    s.remaining = m;
+    s.t_launch = now_seconds();
+    for (Job& j : s.jobs) j.t_launch = s.t_launch;
+    s.busy = true;
+    cudaError_t e = cudaSuccess;
     int rc = POSPOPCNT_OK;
-    if (cfg.per_request) {
+    if (s.single) {
       const Job& j = s.jobs[0];
       rc = pospopcnt_count(width, POSPOPCNT_KERNEL_AUTO, reinterpret_cast<const void*>(j.addr), size_t(j.n),
-                           reinterpret_cast<uint64_t*>(s.d_results), s.stream);
+                           reinterpret_cast<uint64_t*>(s.d_single), s.stream);
+      if (rc == POSPOPCNT_OK &&
+          (e = cudaMemcpyAsync(s.h_single, s.d_single, size_t(width) * 8, cudaMemcpyDeviceToHost, s.stream)) !=
+              cudaSuccess)
+        rc = cuda_fail(e);
     } else {
-      int64_t* hb = reinterpret_cast<int64_t*>(s.h_desc);
-      uint64_t* ha = s.h_desc + (m + 1);
-      hb[0] = 0;
+      ServeArgs args;
+      args.bounds[0] = 0;
+      size_t live = 0;
       for (size_t i = 0; i < m; ++i) {
-        hb[i + 1] = hb[i] + int64_t(s.jobs[i].n);
-        ha[i] = s.jobs[i].addr;
+        args.bounds[i + 1] = args.bounds[i] + int64_t(s.jobs[i].n);
+        args.addr[i] = s.jobs[i].addr;
+        live += s.jobs[i].n > 0;
       }
-      const size_t desc_bytes = (2 * m + 1) * sizeof(uint64_t);
-      if ((e = cudaMemcpyAsync(s.d_desc, s.h_desc, desc_bytes, cudaMemcpyHostToDevice, s.stream)) != cudaSuccess)
-        rc = cuda_fail(e);
-      else if ((e = cudaMemsetAsync(s.d_results, 0, m * size_t(width) * 8, s.stream)) != cudaSuccess)
-        rc = cuda_fail(e);
-      else
-        rc = launch_batched(*st, nullptr, reinterpret_cast<const int64_t*>(s.d_desc), m, width, s.d_results,
-                            s.d_queue, (128 * 1024) / (width / 8), s.stream, s.d_desc + (m + 1));
+      args.nseg = uint32_t(m);
+      args.ticket = ++s.ticket;
+      args.tile_words = uint64_t(SERVE_TILE_BYTES / (width / 8));
+      args.rows = s.d_rows;
+      args.pieces = s.d_pieces;
+      args.h_counts = s.dv_counts;
+      args.h_flags = s.dv_flags;
+      const uint64_t total = uint64_t(args.bounds[m]);
+      // empty jobs have no piece on the device: they complete here
+      for (size_t i = 0; i < m; ++i)
+        if (s.jobs[i].n == 0) {
+          static const unsigned long long zeros[32] = {};
+          finish(s, i, zeros, POSPOPCNT_OK, now_seconds());
+        }
+      if (live) {
+        e = width == 8 ? launch_serve<8>(s, args, total) : width == 16 ? launch_serve<16>(s, args, total)
+                                                                       : launch_serve<32>(s, args, total);
+        if (e != cudaSuccess) rc = cuda_fail(e);
+      }
     }
-    if (rc == POSPOPCNT_OK &&
-        (e = cudaMemcpyAsync(s.h_results, s.d_results, m * size_t(width) * 8, cudaMemcpyDeviceToHost,
-                             s.stream)) != cudaSuccess)
-      rc = cuda_fail(e);
     if (rc == POSPOPCNT_OK && (e = cudaEventRecord(s.done, s.stream)) != cudaSuccess) rc = cuda_fail(e);
-    if (rc != POSPOPCNT_OK) {  // fail the jobs on the host; nothing is in flight for them
+    if (rc != POSPOPCNT_OK) {  // fail the unfinished jobs on the host
       const double td = now_seconds();
-      for (Job& j : s.jobs) {
-        j.t_done = td;
-        adm.release(j.bytes);
-        emit(j, nullptr, rc);
-      }
-      admitted_jobs -= m;
-      s.jobs.clear();
-      return rc;
+      for (size_t i = 0; i < m; ++i)
+        if (!s.finished[i]) finish(s, i, nullptr, rc, td);
     }
-    s.busy = true;
+    if (s.remaining == 0) {
+      s.jobs.clear();
+      s.busy = false;
+    }
     std::lock_guard<std::mutex> lk(stats_mu);
     ++stats.batches;
     stats.jobs_in_batches += m;
     stats.max_batch = std::max<uint64_t>(stats.max_batch, m);
-    return POSPOPCNT_OK;
+    return rc;
   }
 
   bool launch_ready() {
     bool any = false;
     for (Slot& s : slots) {
       if (s.busy) continue;
-      const int wi = oldest_width();
-      if (wi < 0) break;
-      launch(s, wi);
+      const int qi = oldest_queue();
+      if (qi < 0) break;
+      launch(s, qi);
       any = true;
     }
     return any;
@@ -281,7 +430,9 @@ struct Server {
   bool idle() {
     for (const Slot& s : slots)
       if (s.busy) return false;
-    if (!waiting.empty() || !pending[0].empty() || !pending[1].empty() || !pending[2].empty()) return false;
+    if (!waiting.empty() || !pending[0].empty() || !pending[1].empty() || !pending[2].empty() ||
+        !pending_large.empty())
+      return false;
     std::lock_guard<std::mutex> lk(in_mu);
     return incoming.empty();
   }
@@ -314,10 +465,11 @@ int pospopcnt_server_create(int device, const pospopcnt_server_config* cfg_in, p
   pospopcnt_server_config cfg{};
   if (cfg_in) cfg = *cfg_in;
   if (cfg.hbm_budget_bytes == 0) cfg.hbm_budget_bytes = uint64_t(64) << 30;
-  if (cfg.max_inflight == 0) cfg.max_inflight = cfg.per_request ? 64 : 4;
-  if (cfg.max_batch_jobs == 0) cfg.max_batch_jobs = 4096;
+  if (cfg.max_inflight == 0) cfg.max_inflight = cfg.per_request ? 64 : 16;
+  if (cfg.max_batch_jobs == 0) cfg.max_batch_jobs = ppc::SERVE_MAX_JOBS;
   if (cfg.per_request) cfg.max_batch_jobs = 1;
-  if (cfg.max_inflight < 1 || cfg.max_inflight > 256 || cfg.max_batch_jobs < 1 || cfg.max_batch_jobs > 65536)
+  if (cfg.max_inflight < 1 || cfg.max_inflight > 256 || cfg.max_batch_jobs < 1 ||
+      cfg.max_batch_jobs > ppc::SERVE_MAX_JOBS)
     return POSPOPCNT_ERR_INVALID;
   int rc = pospopcnt_init(device);
   if (rc != POSPOPCNT_OK) return rc;
@@ -336,24 +488,38 @@ int pospopcnt_server_create(int device, const pospopcnt_server_config* cfg_in, p
   s.cfg = cfg;
   s.st = st;
   s.adm.budget = cfg.hbm_budget_bytes;
-  const size_t B = size_t(cfg.max_batch_jobs);
-  const size_t desc_bytes = (2 * B + 1) * sizeof(uint64_t);
-  const size_t res_bytes = B * 32 * sizeof(uint64_t);
-  const size_t per_slot = ((desc_bytes + 255) / 256 + (res_bytes + 255) / 256 + 1) * 256;
+  s.large_job_bytes = cfg.large_job_bytes ? cfg.large_job_bytes : (uint64_t(4) << 20);
+  const size_t rows_bytes = size_t(ppc::SERVE_MAX_JOBS) * 32 * sizeof(uint64_t);
+  const size_t pieces_bytes = size_t(ppc::SERVE_MAX_JOBS) * sizeof(unsigned);
+  const size_t pieces_pad = ((pieces_bytes + 255) / 256) * 256;
+  const size_t per_slot = rows_bytes + pieces_pad + 256;       // + the single-job row
+  const size_t host_per_slot = rows_bytes + pieces_pad + 256;  // + its host copy
   s.slots.resize(size_t(cfg.max_inflight));
   if ((e = cudaMalloc(&s.d_pool, per_slot * s.slots.size())) != cudaSuccess) rc = ppc::cuda_fail(e);
   if (rc == POSPOPCNT_OK && (e = cudaMemset(s.d_pool, 0, per_slot * s.slots.size())) != cudaSuccess)
     rc = ppc::cuda_fail(e);
+  if (rc == POSPOPCNT_OK &&
+      (e = cudaHostAlloc(&s.h_pool, host_per_slot * s.slots.size(), cudaHostAllocMapped)) != cudaSuccess)
+    rc = ppc::cuda_fail(e);
+  if (rc == POSPOPCNT_OK) std::memset(s.h_pool, 0, host_per_slot * s.slots.size());
+  void* dv_pool = nullptr;
+  if (rc == POSPOPCNT_OK && (e = cudaHostGetDevicePointer(&dv_pool, s.h_pool, 0)) != cudaSuccess)
+    rc = ppc::cuda_fail(e);
   for (size_t i = 0; rc == POSPOPCNT_OK && i < s.slots.size(); ++i) {
     ppc::Slot& sl = s.slots[i];
     char* base = static_cast<char*>(s.d_pool) + i * per_slot;
-    sl.d_desc = reinterpret_cast<uint64_t*>(base);
-    sl.d_results = reinterpret_cast<unsigned long long*>(base + (desc_bytes + 255) / 256 * 256);
-    sl.d_queue = base + per_slot - 256;
+    sl.d_rows = reinterpret_cast<unsigned long long*>(base);
+    sl.d_pieces = reinterpret_cast<unsigned*>(base + rows_bytes);
+    sl.d_single = reinterpret_cast<unsigned long long*>(base + rows_bytes + pieces_pad);
+    char* hb = static_cast<char*>(s.h_pool) + i * host_per_slot;
+    char* dvb = static_cast<char*>(dv_pool) + i * host_per_slot;
+    sl.h_counts = reinterpret_cast<unsigned long long*>(hb);
+    sl.h_flags = reinterpret_cast<unsigned*>(hb + rows_bytes);
+    sl.h_single = reinterpret_cast<unsigned long long*>(hb + rows_bytes + pieces_pad);
+    sl.dv_counts = reinterpret_cast<unsigned long long*>(dvb);
+    sl.dv_flags = reinterpret_cast<unsigned*>(dvb + rows_bytes);
     if ((e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming)) != cudaSuccess ||
-        (e = cudaHostAlloc(reinterpret_cast<void**>(&sl.h_desc), desc_bytes, cudaHostAllocDefault)) != cudaSuccess ||
-        (e = cudaHostAlloc(reinterpret_cast<void**>(&sl.h_results), res_bytes, cudaHostAllocDefault)) != cudaSuccess)
+        (e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming)) != cudaSuccess)
       rc = ppc::cuda_fail(e);
   }
   cudaSetDevice(prev);
@@ -377,10 +543,9 @@ int pospopcnt_server_destroy(pospopcnt_server* srv) {
   for (ppc::Slot& sl : s.slots) {
     if (sl.stream) cudaStreamSynchronize(sl.stream), cudaStreamDestroy(sl.stream);
     if (sl.done) cudaEventDestroy(sl.done);
-    if (sl.h_desc) cudaFreeHost(sl.h_desc);
-    if (sl.h_results) cudaFreeHost(sl.h_results);
   }
   if (s.d_pool) cudaFree(s.d_pool);
+  if (s.h_pool) cudaFreeHost(s.h_pool);
   cudaSetDevice(prev);
   delete srv;
   return POSPOPCNT_OK;

@@ -61,7 +61,7 @@ def _run(server, dev, tr):
 def test_same_alone_and_in_the_mix(pool):
     host, dev = pool
     tr = _trace(1, rate=20000, duration=0.15, max_bytes=4 << 20)
-    srv = ppc.pospopcnt_server_create(0, max_inflight=4, max_batch_jobs=512)
+    srv = ppc.pospopcnt_server_create(0, max_inflight=8, max_batch_jobs=240)
     try:
         lat, mixed, status = _run(srv, dev, tr)
         st = ppc.pospopcnt_server_get_stats(srv)
@@ -95,7 +95,9 @@ def test_per_request_mode_same_results(pool):
 def test_budget_defers_and_holds(pool):
     host, dev = pool
     budget = 3 << 20
-    tr = _trace(3, rate=50000, duration=0.02, max_bytes=1 << 20)
+    # a burst: ~400 requests (~60 MB) arriving within 4 microseconds
+    tr = _trace(3, rate=1e8, duration=4e-6, max_bytes=1 << 20)
+    assert tr["t_arrival"].size > 100
     srv = ppc.pospopcnt_server_create(0, hbm_budget_bytes=budget, max_inflight=4, max_batch_jobs=64)
     try:
         lat, counts, status = _run(srv, dev, tr)
@@ -138,3 +140,21 @@ def test_submit_poll_and_rejection(pool):
         assert r["status"] == 0 and r["width"] == w
         assert r["t_arrival"] <= r["t_admit"] <= r["t_launch"] <= r["t_done"]
         assert np.array_equal(r["counts"], oracle.pospopcnt(host[a:a + nb], w))
+
+
+def test_mixed_routes_same_results(pool):
+    """Small jobs batched and large jobs on their own launches, in one mix."""
+    host, dev = pool
+    tr = _trace(5, rate=20000, duration=0.1, max_bytes=8 << 20)
+    srv = ppc.pospopcnt_server_create(0, max_inflight=8, large_job_bytes=256 << 10)
+    try:
+        lat, mixed, status = _run(srv, dev, tr)
+        st = ppc.pospopcnt_server_get_stats(srv)
+    finally:
+        ppc.pospopcnt_server_destroy(srv)
+    assert np.all(status == 0)
+    nbytes = tr["nwords"].astype(np.int64) * (tr["width"] // 8)
+    assert np.any(nbytes >= 256 << 10) and np.any(nbytes < 256 << 10)
+    assert np.array_equal(mixed, _oracle_rows(host, tr))
+    assert np.array_equal(mixed, _solo_rows(dev, tr))
+    assert st["completed"] == tr["t_arrival"].size
