@@ -383,7 +383,7 @@ def run_batched(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     ppc.pospopcnt_init(local)
-    nseg = 20000
+    nseg = args.batched_nseg
     lens = synth.log_uniform_lengths(rank, nseg)
     off = synth.offsets_from_lengths(lens)
     words = synth.segmented_one_hot(rank, off, 16)
@@ -652,6 +652,7 @@ def main(argv=None):
     p.add_argument("--workload", default="u16",
                    choices=["u16", "u16_onehot", "u16_sparse", "u16_misaligned", "u8", "u32", "sweep", "batched",
                             "kernels", "autotune", "serve"])
+    p.add_argument("--batched-nseg", type=int, default=20000)
     p.add_argument("--serve-rate", type=float, default=50000.0)
     p.add_argument("--serve-seconds", type=float, default=60.0)
     p.add_argument("--serve-slots", type=int, default=16, help="batches in flight (continuous batching)")

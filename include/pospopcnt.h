@@ -105,13 +105,20 @@ int pospopcnt_count_config(int width, const pospopcnt_config* cfg, const void* d
 int pospopcnt_count_accumulate(int width, const void* d_in, size_t n, uint64_t* d_counts,
                                cudaStream_t stream);
 
-/* pospopcnt of HOST memory: copies h_in (n words, pinned or pageable) to the
- * device in chunks through the library's staging buffers, overlapping the
- * copies with counting on two streams, and writes the width uint64 counts to
- * h_counts (host memory).  Synchronous: returns when h_counts is written.
- * The first call on a device allocates the staging buffers
- * (2 x 64 MiB) and two streams. */
+/* pospopcnt of HOST memory (n words at h_in); writes the width uint64
+ * counts to h_counts (host memory).  Synchronous: returns when h_counts is
+ * written.  If the whole range is pinned host memory mapped into the
+ * device's address space (cudaHostAlloc / cudaHostRegister with mapping),
+ * the kernel reads it in place across the CPU-GPU link; otherwise the bytes
+ * are copied to the device in chunks through the library's staging buffers,
+ * overlapping the copies with counting on two streams.  The first call on a
+ * device allocates the staging buffers (2 x 64 MiB) and two streams. */
 int pospopcnt_count_host(int width, const void* h_in, size_t n, uint64_t* h_counts);
+
+/* 1 if pospopcnt_count_host would read [h_in, h_in + nbytes) in place
+ * (the whole range is pinned host memory mapped into the current device's
+ * address space), 0 if it would copy it through the staging buffers. */
+int pospopcnt_host_is_mapped(const void* h_in, size_t nbytes);
 
 /* Segmented pospopcnt (one persistent launch over all segments).
  * Segment s covers words [d_offsets[s], d_offsets[s+1]) of d_in; row s of

@@ -23,6 +23,7 @@ from . import _build
 __all__ = [
     "PospopcntError", "load", "pospopcnt_init", "pospopcnt_u8", "pospopcnt_u16", "pospopcnt_u32",
     "pospopcnt_count", "pospopcnt_count_config", "pospopcnt_count_accumulate", "pospopcnt_count_host",
+    "pospopcnt_host_is_mapped",
     "pospopcnt_batched", "pospopcnt_batched_noalloc", "pospopcnt_plain_segments", "pospopcnt_check_device_error", "pospopcnt_plan_split",
     "pospopcnt_get_config", "pospopcnt_set_config", "pospopcnt_autotune", "pospopcnt_strerror",
     "pospopcnt_last_cuda_error", "pospopcnt_launch_count", "pospopcnt_selftest_timeout", "KERNELS",
@@ -113,6 +114,7 @@ def _declare(lib):
         "pospopcnt_count_config": (i32, [i32, P(Config), vp, sz, vp, vp]),
         "pospopcnt_count_accumulate": (i32, [i32, vp, sz, vp, vp]),
         "pospopcnt_count_host": (i32, [i32, vp, sz, vp]),
+        "pospopcnt_host_is_mapped": (i32, [vp, sz]),
         "pospopcnt_batched": (i32, [vp, vp, sz, i32, vp, vp]),
         "pospopcnt_plain_segments": (i32, [vp, vp, sz, i32, vp, vp]),
         "pospopcnt_batched_noalloc": (i32, [vp, vp, sz, i32, vp, vp]),
@@ -271,6 +273,16 @@ def pospopcnt_count_host(width: int, h, out: np.ndarray | None = None) -> np.nda
     _check(_lib().pospopcnt_count_host(width, ptr, nbytes // (width // 8), out.ctypes.data),
            "pospopcnt_count_host")
     return out
+
+
+def pospopcnt_host_is_mapped(h) -> bool:
+    """Whether pospopcnt_count_host reads host buffer h in place."""
+    if hasattr(h, "data_ptr"):
+        ptr, nbytes = h.data_ptr(), h.numel() * h.element_size()
+    else:
+        a = np.ascontiguousarray(h)
+        ptr, nbytes = a.ctypes.data, a.nbytes
+    return bool(_lib().pospopcnt_host_is_mapped(ctypes.c_void_p(ptr), nbytes))
 
 
 def pospopcnt_batched(x, offsets, width: int, counts=None, stream=None):

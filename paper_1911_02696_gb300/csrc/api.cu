@@ -207,7 +207,38 @@ int launch_plain(const DeviceState& st, int width, const pospopcnt_config& cfg, 
   return POSPOPCNT_ERR_INVALID;
 }
 
+template <int K>
+int launch_plain_sysmem_k(const DeviceState&, const void*, size_t, unsigned long long*, cudaStream_t);
+
+int launch_plain_sysmem(const DeviceState& st, int width, const void* d_in, size_t n, unsigned long long* d_counts,
+                        cudaStream_t stream) {
+  switch (width) {
+    case 8: return launch_plain_sysmem_k<8>(st, d_in, n, d_counts, stream);
+    case 16: return launch_plain_sysmem_k<16>(st, d_in, n, d_counts, stream);
+    case 32: return launch_plain_sysmem_k<32>(st, d_in, n, d_counts, stream);
+  }
+  return POSPOPCNT_ERR_INVALID;
+}
+
 namespace {
+
+// Device address of [h, h + bytes) if the whole range is pinned host memory
+// mapped into the current device's address space, else nullptr.
+const void* mapped_device_view(const void* h, size_t bytes) {
+  if (bytes == 0) return nullptr;
+  cudaPointerAttributes a0, a1;
+  const char* last = static_cast<const char*>(h) + bytes - 1;
+  if (cudaPointerGetAttributes(&a0, h) != cudaSuccess || cudaPointerGetAttributes(&a1, last) != cudaSuccess) {
+    cudaGetLastError();  // clear the sticky-free error of an unregistered pointer
+    return nullptr;
+  }
+  if (a0.type != cudaMemoryTypeHost || a1.type != cudaMemoryTypeHost || !a0.devicePointer || !a1.devicePointer)
+    return nullptr;
+  if (static_cast<const char*>(a1.devicePointer) - static_cast<const char*>(a0.devicePointer) !=
+      static_cast<ptrdiff_t>(bytes - 1))
+    return nullptr;
+  return a0.devicePointer;
+}
 
 int check_args(int width, const void* d_in, size_t n, const void* d_counts) {
   if (width_index(width) < 0) return POSPOPCNT_ERR_INVALID;
@@ -298,6 +329,17 @@ int pospopcnt_count_host(int width, const void* h_in, size_t n, uint64_t* h_coun
   }
   cudaStream_t s0 = st->hstream[0], s1 = st->hstream[1];
   const size_t wb = size_t(width / 8);
+  // pinned, mapped host memory: the kernel reads it in place across C2C
+  if (const void* dview = mapped_device_view(h_in, n * wb)) {
+    if ((e = cudaMemsetAsync(st->d_acc, 0, sizeof(uint64_t) * size_t(width), s0)) != cudaSuccess)
+      return cuda_fail(e);
+    if ((rc = launch_plain_sysmem(*st, width, dview, n, st->d_acc, s0)) != POSPOPCNT_OK) return rc;
+    if ((e = cudaMemcpyAsync(h_counts, st->d_acc, sizeof(uint64_t) * size_t(width), cudaMemcpyDeviceToHost,
+                             s0)) != cudaSuccess)
+      return cuda_fail(e);
+    if ((e = cudaStreamSynchronize(s0)) != cudaSuccess) return cuda_fail(e);
+    return POSPOPCNT_OK;
+  }
   const size_t chunk_words = HOST_STAGE_BYTES / wb;
   const pospopcnt_config cfg = config_for(*st, width, chunk_words);
   if ((e = cudaMemsetAsync(st->d_acc, 0, sizeof(uint64_t) * size_t(width), s0)) != cudaSuccess)
@@ -322,6 +364,12 @@ int pospopcnt_count_host(int width, const void* h_in, size_t n, uint64_t* h_coun
     return cuda_fail(e);
   if ((e = cudaStreamSynchronize(s0)) != cudaSuccess) return cuda_fail(e);
   return POSPOPCNT_OK;
+}
+
+int pospopcnt_host_is_mapped(const void* h_in, size_t nbytes) {
+  int rc = POSPOPCNT_OK;
+  if (!current_state(&rc)) return 0;
+  return mapped_device_view(h_in, nbytes) ? 1 : 0;
 }
 
 int pospopcnt_batched(const void* d_in, const int64_t* d_offsets, size_t nseg, int width, uint64_t* d_counts,

@@ -121,6 +121,16 @@ __device__ __forceinline__ uint4 ld_stream(const uint4* p) {
   return r;
 }
 
+// Plain coherent 16-byte load, for inputs that live in pinned host memory
+// mapped into the device address space (read across NVLink-C2C).
+__device__ __forceinline__ uint4 ld_coherent(const uint4* p) {
+  uint4 r;
+  asm volatile("ld.global.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+               : "l"(p));
+  return r;
+}
+
 // ---- warp reduction of K position counters --------------------------------
 // Transpose-reduce: at each step with lane offset `off` a lane keeps one
 // half of its m values, sends the other half to its partner and adds what it

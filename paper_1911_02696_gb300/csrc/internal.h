@@ -52,6 +52,11 @@ Split plan_split(int width, uint64_t addr, size_t n);
 int launch_plain(const DeviceState& st, int width, const pospopcnt_config& cfg, const void* d_in,
                  size_t n, unsigned long long* d_counts, bool zero_first, cudaStream_t stream);
 
+// Count of n words in pinned host memory mapped into the device address
+// space (d_in: its device address), adding into d_counts.
+int launch_plain_sysmem(const DeviceState& st, int width, const void* d_in, size_t n,
+                        unsigned long long* d_counts, cudaStream_t stream);
+
 // Validates a configuration for a width; fills defaults for zero fields.
 int normalize_config(const DeviceState& st, int width, pospopcnt_config* cfg);
 

@@ -48,7 +48,9 @@ __device__ __forceinline__ void count_head_tail(uint32_t (&c)[K], const PlainArg
 }
 
 // ---------------------------------------------------------------------------
-template <int K, int U, int NTHREADS>
+// SYSMEM: the input is pinned host memory mapped into the device's address
+// space; it is read with plain coherent loads instead of the read-only path.
+template <int K, int U, int NTHREADS, bool SYSMEM = false>
 __global__ void __launch_bounds__(NTHREADS) csa_kernel(PlainArgs a) {
   constexpr int R = 4 * U;
   constexpr int L = ilog2<R>::value;
@@ -67,7 +69,7 @@ __global__ void __launch_bounds__(NTHREADS) csa_kernel(PlainArgs a) {
     uint32_t d[R];
 #pragma unroll
     for (int i = 0; i < U; ++i) {
-      const uint4 x = ld_stream(a.body + v + i * stride);
+      const uint4 x = SYSMEM ? ld_coherent(a.body + v + i * stride) : ld_stream(a.body + v + i * stride);
       d[4 * i + 0] = x.x, d[4 * i + 1] = x.y, d[4 * i + 2] = x.z, d[4 * i + 3] = x.w;
     }
     flush<K>(top, Circuit<L>::run(d, B));
@@ -77,7 +79,8 @@ __global__ void __launch_bounds__(NTHREADS) csa_kernel(PlainArgs a) {
 #pragma unroll
     for (int i = 0; i < U; ++i) {
       const uint64_t idx = v + i * stride;
-      const uint4 x = idx < a.nvec ? ld_stream(a.body + idx) : make_uint4(0, 0, 0, 0);
+      const uint4 x = idx < a.nvec ? (SYSMEM ? ld_coherent(a.body + idx) : ld_stream(a.body + idx))
+                                   : make_uint4(0, 0, 0, 0);
       d[4 * i + 0] = x.x, d[4 * i + 1] = x.y, d[4 * i + 2] = x.z, d[4 * i + 3] = x.w;
     }
     flush<K>(top, Circuit<L>::run(d, B));
@@ -271,9 +274,9 @@ static int prepare_counts(PlainArgs& a, uint64_t grid, bool zero_first, cudaStre
   return POSPOPCNT_OK;
 }
 
-template <int K, int U, int T>
+template <int K, int U, int T, bool SYSMEM = false>
 static int launch_csa(const DeviceState& st, PlainArgs a, int bps, bool zero_first, cudaStream_t stream) {
-  auto kern = csa_kernel<K, U, T>;
+  auto kern = csa_kernel<K, U, T, SYSMEM>;
   const int occ = occupancy(kern, T, 0);
   const uint64_t cap = uint64_t(st.sms) * uint64_t(std::min(bps > 0 ? bps : occ, occ));
   const uint64_t need = (a.nvec + uint64_t(U) * T - 1) / (uint64_t(U) * T);
@@ -336,6 +339,33 @@ static int launch_csa_u(const DeviceState& st, const PlainArgs& a, const pospopc
     case 8: return launch_csa<K, 8, T>(st, a, cfg.blocks_per_sm, zero_first, stream);
   }
   return POSPOPCNT_ERR_INVALID;
+}
+
+template <int K>
+static PlainArgs make_args(const DeviceState& st, const void* d_in, size_t n, unsigned long long* d_counts) {
+  const Split sp = plan_split(K, reinterpret_cast<uint64_t>(d_in), n);
+  const uint8_t* base = static_cast<const uint8_t*>(d_in);
+  PlainArgs a;
+  a.head = base;
+  a.head_words = uint32_t(sp.head_words);
+  a.body = reinterpret_cast<const uint4*>(base + sp.head_words * (K / 8));
+  a.nvec = sp.body_vectors;
+  a.tail = base + sp.head_words * (K / 8) + sp.body_vectors * 16;
+  a.tail_words = uint32_t(sp.tail_words);
+  a.counts = d_counts;
+  a.err = st.d_err;
+  a.store = 0;
+  return a;
+}
+
+// Count of words in pinned host memory mapped into the device address space
+// (d_in is its device address); adds into d_counts.
+template <int K>
+int launch_plain_sysmem_k(const DeviceState& st, const void* d_in, size_t n, unsigned long long* d_counts,
+                          cudaStream_t stream) {
+  PlainArgs a = make_args<K>(st, d_in, n, d_counts);
+  if (a.nvec == 0 && a.head_words == 0 && a.tail_words == 0) return POSPOPCNT_OK;
+  return launch_csa<K, 4, 256, true>(st, a, 0, false, stream);
 }
 
 template <int K>
