@@ -613,6 +613,48 @@ def run_serve(args, world, rank, local):
             "results_same_alone_and_in_mix": same, "batched_equals_per_request_all": same_all}
 
 
+def run_e2e(args, world, rank, local):
+    """Host-buffer counting of 2^30 u16 words: pinned memory read in place,
+    pageable memory through the staging copies, and a plain pinned copy to
+    the device (the link reference), all through public calls."""
+    import torch
+    import oracle
+    import paper_1911_02696_gb300 as ppc
+    import synth
+    torch.cuda.set_device(local)
+    ppc.pospopcnt_init(local)
+    words = synth.uniform_bits(rank, 1 << 30, 16)
+    nbytes = words.nbytes
+    pinned = torch.from_numpy(words.view(np.uint8)).pin_memory()
+    dev = torch.empty(nbytes, dtype=torch.uint8, device=torch.device("cuda", local))
+
+    def rate(f, reps):
+        f()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            f()
+        return nbytes * reps / (time.perf_counter() - t0) / 1e9
+
+    def copy():
+        dev.copy_(pinned, non_blocking=True)
+        torch.cuda.synchronize()
+    k = max(2, min(args.steps, 10))
+    res = {"pinned_in_place_GBps": round(rate(lambda: ppc.pospopcnt_count_host(16, pinned), k), 2),
+           "pinned_is_mapped": ppc.pospopcnt_host_is_mapped(pinned),
+           "pageable_staged_GBps": round(rate(lambda: ppc.pospopcnt_count_host(16, words), max(2, k // 2)), 2),
+           "memcpy_pinned_GBps": round(rate(copy, k), 2)}
+    ref, _ = oracle.pospopcnt_mt(words, 16)
+    res["bit_exact"] = bool(np.array_equal(ppc.pospopcnt_count_host(16, pinned), ref) and
+                            np.array_equal(ppc.pospopcnt_count_host(16, words), ref))
+    if rank != 0:
+        return None
+    return {"metric": "pospopcnt_u16 GB/s from host memory", "value": res["pinned_in_place_GBps"], "unit": UNIT,
+            "n_gpus": world, "steps": k, "warmup": 1, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+            "config": {"workload": "pospopcnt_count_host, n=2^30 u16 words (2 GiB) in host memory"}, **res,
+            "frac_of_link": round(res["pinned_in_place_GBps"] / res["memcpy_pinned_GBps"], 4)}
+
+
 def run_reference(args, world, rank):
     """The reference arm: the scalar CPU oracle on the host cores, each step
     a bounded 2^26-word sample of the same workload."""
@@ -651,7 +693,7 @@ def main(argv=None):
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="u16",
                    choices=["u16", "u16_onehot", "u16_sparse", "u16_misaligned", "u8", "u32", "sweep", "batched",
-                            "kernels", "autotune", "serve"])
+                            "kernels", "autotune", "serve", "e2e"])
     p.add_argument("--batched-nseg", type=int, default=20000)
     p.add_argument("--serve-rate", type=float, default=50000.0)
     p.add_argument("--serve-seconds", type=float, default=60.0)
@@ -685,6 +727,8 @@ def main(argv=None):
             out = run_autotune(args, world, rank, local)
         elif args.workload == "serve":
             out = run_serve(args, world, rank, local)
+        elif args.workload == "e2e":
+            out = run_e2e(args, world, rank, local)
         else:
             out = run_plain(args, world, rank, local)
         if world > 1:

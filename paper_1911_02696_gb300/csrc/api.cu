@@ -400,7 +400,7 @@ int pospopcnt_batched(const void* d_in, const int64_t* d_offsets, size_t nseg, i
   cudaError_t e = cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * size_t(width) * nseg, stream);
   if (e != cudaSuccess) return cuda_fail(e);
   void* q = static_cast<char*>(st->d_queue) + size_t(slot) * QUEUE_SLOT_BYTES;
-  const int tile_words = (128 * 1024) / (width / 8);  // 128 KiB of input per tile
+  const int tile_words = (16 * 1024) / (width / 8);  // 16 KiB scheduling unit
   return launch_batched(*st, d_in, d_offsets, nseg, width, reinterpret_cast<unsigned long long*>(d_counts), q,
                         tile_words, stream);
 }

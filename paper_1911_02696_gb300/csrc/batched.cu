@@ -1,14 +1,15 @@
 // Segmented pospopcnt in one persistent launch.
 //
 // Segment s covers words [offsets[s], offsets[s+1]).  The word range
-// [offsets[0], offsets[nseg]) is cut into tiles of `tile_words` words whose
-// inner boundaries fall on 16-byte addresses.  Persistent CTAs pop tile
-// indices from an atomic work queue; a CTA splits its tile into one
-// contiguous sub-range per warp.  A warp finds the segment holding the first
-// word of its sub-range with a 32-way search over the offsets, then walks the
-// pieces (segment ∩ sub-range): each piece is counted like a plain call --
+// [offsets[0], offsets[nseg]) is cut into units of `tile_words` words whose
+// inner boundaries fall on 16-byte addresses.  Every warp of a persistent
+// grid claims runs of consecutive units from an atomic work queue (guided
+// self-scheduling: about 1/(2 x warps) of what is left, at least one unit),
+// so no warp waits for another.  A warp finds the segment holding the first
+// word of its run with a 32-way search over the offsets, then walks the
+// pieces (segment ∩ run): each piece is counted like a plain call --
 // unaligned head and ragged tail word by word, the body in 16-byte vectors
-// through the carry-save circuit F_4 (§2, §4.1) with popc flushes -- and its
+// through the carry-save circuit F_5 (§2, §4.1) with popc flushes -- and its
 // counts are reduced across the warp and added with one 64-bit atomic per
 // position into the segment's row.  Rows are zeroed beforehand by a memset.
 //
@@ -49,29 +50,42 @@ __device__ __forceinline__ void warp_count_piece(const uint8_t* base, uint64_t p
                                                  unsigned long long* row) {
   constexpr int SH = 5 - ilog2<K>::value;
   const int lane = threadIdx.x & 31;
-  const uint32_t v = warp_piece_counts<K>(base, pa, pb);
+  const uint32_t v = warp_piece_counts<K, BT_VPL>(base, pa, pb);
   if ((lane & ((1 << SH) - 1)) == 0 && v) atomicAdd(row + (lane >> SH), (unsigned long long)v);
 }
 
 template <int K>
-__global__ void __launch_bounds__(BT_THREADS, bt_min_blocks<K>::value) batched_kernel(BatchedArgs a) {
+__global__ void __launch_bounds__(BT_THREADS, bt_batched_min_blocks<K>::value) batched_kernel(BatchedArgs a) {
   constexpr int WB = K / 8;
-  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   const int64_t o0 = a.offsets[0];
   const int64_t oN = a.offsets[a.nseg];
-  // offsets form: the first tile starts at the 16-byte boundary at or before
-  // word o0, so inner tile boundaries are aligned; descriptor form: at o0
+  // offsets form: units start at the 16-byte boundary at or before word o0,
+  // so inner unit boundaries are aligned; descriptor form: at o0
   const uint64_t mis =
       a.seg_addr ? 0 : (reinterpret_cast<uint64_t>(a.base) + uint64_t(o0) * WB) & 15;
   const int64_t start = o0 - int64_t(mis / WB);
-  const uint64_t T = a.tile_words, Tw = a.tile_words / BT_WARPS;
+  const uint64_t U = a.tile_words;  // words per scheduling unit
+  const uint64_t units = oN > start ? (uint64_t(oN - start) + U - 1) / U : 0;
+  const uint64_t nwarps = uint64_t(gridDim.x) * BT_WARPS;
 
+  // Guided self-scheduling per warp: take about 1/(2 nwarps) of the units
+  // still unclaimed (at least one), so early grabs are large, late ones
+  // small, and no warp waits for another.
   for (;;) {
-    const uint64_t tile = pop_tile(a.q);
-    if (oN <= start || tile >= (uint64_t(oN - start) + T - 1) / T) break;
-    const int64_t t0 = start + int64_t(tile * T);
-    int64_t w0 = t0 + int64_t(warp * Tw);
-    int64_t w1 = w0 + int64_t(Tw);
+    uint64_t u0 = 0, u1 = 0;
+    if (lane == 0) {
+      const uint64_t seen = *reinterpret_cast<volatile unsigned long long*>(&a.q->next);
+      const uint64_t left = seen < units ? units - seen : 0;
+      const uint64_t k = left / (2 * nwarps) > 1 ? left / (2 * nwarps) : 1;
+      u0 = atomicAdd(&a.q->next, (unsigned long long)k);
+      u1 = u0 + k < units ? u0 + k : units;
+    }
+    u0 = __shfl_sync(FULL_MASK, u0, 0);
+    u1 = __shfl_sync(FULL_MASK, u1, 0);
+    if (u0 >= units) break;
+    int64_t w0 = start + int64_t(u0 * U);
+    int64_t w1 = start + int64_t(u1 * U);
     if (w0 < o0) w0 = o0;
     if (w1 > oN) w1 = oN;
     if (w0 >= w1) continue;
@@ -210,7 +224,7 @@ extern "C" int pospopcnt_batched_noalloc(const void* d_in, const int64_t* d_offs
   a.nseg = nseg;
   a.counts = reinterpret_cast<unsigned long long*>(d_counts);
   a.q = static_cast<QueueSlot*>(scratch);
-  a.tile_words = uint64_t((128 * 1024) / (width / 8));
+  a.tile_words = uint64_t((16 * 1024) / (width / 8));
   switch (width) {
     case 8: return launch_batched_k<8>(st, a, stream);
     case 16: return launch_batched_k<16>(st, a, stream);

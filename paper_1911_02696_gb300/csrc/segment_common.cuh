@@ -23,6 +23,12 @@ template <int K>
 struct bt_min_blocks {
   static constexpr int value = K == 32 ? 3 : 5;
 };
+// the batched kernel's trips carry 8 vectors per lane: fewer, fuller warps
+constexpr int BT_VPL = 8;
+template <int K>
+struct bt_batched_min_blocks {
+  static constexpr int value = K == 32 ? 3 : 4;
+};
 
 // Pops the next tile index for the CTA (every thread gets it).
 __device__ __forceinline__ uint64_t pop_tile(QueueSlot* q) {
@@ -70,11 +76,14 @@ __device__ __forceinline__ uint64_t find_segment(const int64_t* bounds, uint64_t
 }
 
 // Counts words [pa, pb) of `base` with the whole warp: the unaligned head
-// and ragged tail word by word, the 16-byte body through F_4 with popc
-// flushes.  Returns, in lanes with (lane & (2^(5 - log2 K) - 1)) == 0, the
-// warp total of position lane >> (5 - log2 K); other lanes return partials.
-template <int K>
+// and ragged tail word by word, the 16-byte body in trips of VPL vectors per
+// lane through F_{log2 4 VPL} with popc flushes.  Returns, in lanes with
+// (lane & (2^(5 - log2 K) - 1)) == 0, the warp total of position
+// lane >> (5 - log2 K); other lanes return partials.
+template <int K, int VPL = 4>
 __device__ __forceinline__ uint32_t warp_piece_counts(const uint8_t* base, uint64_t pa, uint64_t pb) {
+  constexpr int R = 4 * VPL;
+  constexpr int L = ilog2<R>::value;
   constexpr int WB = K / 8;
   const int lane = threadIdx.x & 31;
   const uint64_t A = reinterpret_cast<uint64_t>(base) + pa * WB;
@@ -94,23 +103,25 @@ __device__ __forceinline__ uint32_t warp_piece_counts(const uint8_t* base, uint6
   else if (lane >= 16 && uint32_t(lane - 16) < tail_words)
     edge = load_word<K>(reinterpret_cast<const uint8_t*>(bodyE) + (lane - 16) * WB);
 
-  uint32_t B[4] = {0, 0, 0, 0};
+  uint32_t B[L];
+#pragma unroll
+  for (int l = 0; l < L; ++l) B[l] = 0;
   uint32_t top[K];
 #pragma unroll
   for (int p = 0; p < K; ++p) top[p] = 0;
   const uint4* vp = reinterpret_cast<const uint4*>(bodyA);
-  for (uint64_t bv = 0; bv < nvec; bv += 128) {  // 32 lanes x 4 vectors per trip
-    uint32_t d[16];
+  for (uint64_t bv = 0; bv < nvec; bv += 32 * VPL) {  // 32 lanes x VPL vectors per trip
+    uint32_t d[R];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < VPL; ++j) {
       const uint64_t idx = bv + uint64_t(j) * 32 + lane;
       const uint4 x = idx < nvec ? ld_stream(vp + idx) : make_uint4(0, 0, 0, 0);
       d[4 * j + 0] = x.x, d[4 * j + 1] = x.y, d[4 * j + 2] = x.z, d[4 * j + 3] = x.w;
     }
-    flush<K>(top, Circuit<4>::run(d, B));
+    flush<K>(top, Circuit<L>::run(d, B));
   }
   uint32_t c[K];
-  finalize<K, 4>(c, top, B);
+  finalize<K, L>(c, top, B);
   count_word<K>(c, edge);
   return warp_reduce_positions<K>(c);
 }
