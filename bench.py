@@ -245,7 +245,13 @@ def run_plain(args, world, rank, local):
     x.copy_(host)
     counts = torch.empty(width, dtype=torch.int64, device=dev)
     ppc.pospopcnt_init(local)
-    fn = {8: ppc.pospopcnt_u8, 16: ppc.pospopcnt_u16, 32: ppc.pospopcnt_u32}[width]
+    if args.kernel:  # a named kernel family in its default configuration (comparison / profiling)
+        fixed = {"kernel": args.kernel}
+
+        def fn(t, counts):
+            return ppc.pospopcnt_count_config(width, fixed, t, counts=counts)
+    else:
+        fn = {8: ppc.pospopcnt_u8, 16: ppc.pospopcnt_u16, 32: ppc.pospopcnt_u32}[width]
     stream = torch.cuda.current_stream(dev)
 
     # correctness of the timed configuration (oracle on rank 0's host copy is
@@ -296,6 +302,8 @@ def run_plain(args, world, rank, local):
     launch_ms = statistics.mean(per_step)
     achieved = (nbytes + width * 8) / (launch_ms * 1e-3) / 1e9
     cfg = ppc.pospopcnt_get_config(width, words.size)
+    if args.kernel:
+        cfg = {"kernel": ppc.KERNELS[args.kernel], "note": "library default launch for this family"}
     kname = {1: "csa", 2: "tma", 3: "ballot"}[cfg["kernel"]]
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_source": f"{peak_src} (copy bandwidth)",
@@ -702,6 +710,8 @@ def main(argv=None):
     p.add_argument("--serve-large-mib", type=float, default=4.0,
                    help="jobs at least this large are launched on their own")
     p.add_argument("--e2e-steps", type=int, default=10)
+    p.add_argument("--kernel", choices=["csa", "tma", "ballot"], default=None,
+                   help="time one kernel family instead of the tuned default")
     p.add_argument("--log2-words", type=int, default=None,
                    help="run a smaller uniform-bits case of 2^k words (profiling only)")
     p.add_argument("--no-e2e", action="store_true")
