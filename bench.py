@@ -194,7 +194,7 @@ def make_input(kind: str, seed: int, log2_words: int | None = None):
     """(host words, width, start offset in bytes, description)."""
     import synth
     if log2_words is not None:  # a smaller case of the same workload (profiling)
-        width = {"u8": 8, "u32": 32}.get(kind, 16)
+        width = {"u8": 8, "u32": 32, "u64": 64}.get(kind, 16)
         return (synth.uniform_bits(seed, 1 << log2_words, width), width, 0,
                 f"pospopcnt_u{width} n=2^{log2_words} uniform random bits")
     if kind == "u16":
@@ -208,6 +208,8 @@ def make_input(kind: str, seed: int, log2_words: int | None = None):
                 "pospopcnt_u16 n=2^30+7 uniform bits, start 2 bytes past a 256-byte boundary")
     if kind == "u8":
         return synth.uniform_bits(seed, 1 << 31, 8), 8, 0, "pospopcnt_u8 n=2^31 uniform random bits (2 GiB)"
+    if kind == "u64":
+        return synth.uniform_bits(seed, 1 << 28, 64), 64, 0, "pospopcnt_u64 n=2^28 uniform random bits (2 GiB)"
     if kind == "u32":
         return synth.uniform_bits(seed, 1 << 29, 32), 32, 0, "pospopcnt_u32 n=2^29 uniform random bits (2 GiB)"
     raise ValueError(kind)
@@ -251,7 +253,7 @@ def run_plain(args, world, rank, local):
         def fn(t, counts):
             return ppc.pospopcnt_count_config(width, fixed, t, counts=counts)
     else:
-        fn = {8: ppc.pospopcnt_u8, 16: ppc.pospopcnt_u16, 32: ppc.pospopcnt_u32}[width]
+        fn = {8: ppc.pospopcnt_u8, 16: ppc.pospopcnt_u16, 32: ppc.pospopcnt_u32, 64: ppc.pospopcnt_u64}[width]
     stream = torch.cuda.current_stream(dev)
 
     # correctness of the timed configuration (oracle on rank 0's host copy is
@@ -700,7 +702,7 @@ def main(argv=None):
     p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="u16",
-                   choices=["u16", "u16_onehot", "u16_sparse", "u16_misaligned", "u8", "u32", "sweep", "batched",
+                   choices=["u16", "u16_onehot", "u16_sparse", "u16_misaligned", "u8", "u32", "u64", "sweep", "batched",
                             "kernels", "autotune", "serve", "e2e"])
     p.add_argument("--batched-nseg", type=int, default=20000)
     p.add_argument("--serve-rate", type=float, default=50000.0)

@@ -89,6 +89,14 @@ int pospopcnt_u8(const void* d_in, size_t n, uint64_t* d_counts, cudaStream_t st
 int pospopcnt_u16(const void* d_in, size_t n, uint64_t* d_counts, cudaStream_t stream);
 int pospopcnt_u32(const void* d_in, size_t n, uint64_t* d_counts, cudaStream_t stream);
 
+/* The same for 64-bit words (64 counts; d_in 8-byte aligned).  Wider words
+ * are narrower streams side by side (§4): in each 16-byte vector the 32-bit
+ * registers alternate between positions 0..31 and 32..63, and each thread
+ * runs one carry-save circuit per class.  pospopcnt_count / _config /
+ * _accumulate / _count_host also take width 64 (CSA kernel family only);
+ * the batched and serving forms take 8, 16 or 32. */
+int pospopcnt_u64(const void* d_in, size_t n, uint64_t* d_counts, cudaStream_t stream);
+
 /* The same for width 8, 16 or 32 with an explicit kernel family
  * (pospopcnt_kernel). */
 int pospopcnt_count(int width, int kernel, const void* d_in, size_t n, uint64_t* d_counts,

@@ -21,7 +21,7 @@ import numpy as np
 from . import _build
 
 __all__ = [
-    "PospopcntError", "load", "pospopcnt_init", "pospopcnt_u8", "pospopcnt_u16", "pospopcnt_u32",
+    "PospopcntError", "load", "pospopcnt_init", "pospopcnt_u8", "pospopcnt_u16", "pospopcnt_u32", "pospopcnt_u64",
     "pospopcnt_count", "pospopcnt_count_config", "pospopcnt_count_accumulate", "pospopcnt_count_host",
     "pospopcnt_host_is_mapped",
     "pospopcnt_batched", "pospopcnt_batched_noalloc", "pospopcnt_plain_segments", "pospopcnt_check_device_error", "pospopcnt_plan_split",
@@ -110,6 +110,7 @@ def _declare(lib):
         "pospopcnt_u8": (i32, [vp, sz, vp, vp]),
         "pospopcnt_u16": (i32, [vp, sz, vp, vp]),
         "pospopcnt_u32": (i32, [vp, sz, vp, vp]),
+        "pospopcnt_u64": (i32, [vp, sz, vp, vp]),
         "pospopcnt_count": (i32, [i32, i32, vp, sz, vp, vp]),
         "pospopcnt_count_config": (i32, [i32, P(Config), vp, sz, vp, vp]),
         "pospopcnt_count_accumulate": (i32, [i32, vp, sz, vp, vp]),
@@ -211,6 +212,11 @@ def pospopcnt_u16(x, counts=None, stream=None):
 def pospopcnt_u32(x, counts=None, stream=None):
     """Counts of the 32-bit words of CUDA tensor x (int64[32])."""
     return _plain("pospopcnt_u32", 32, x, counts, stream)
+
+
+def pospopcnt_u64(x, counts=None, stream=None):
+    """Counts of the 64-bit words of CUDA tensor x (int64[64])."""
+    return _plain("pospopcnt_u64", 64, x, counts, stream)
 
 
 def pospopcnt_count(width: int, x, kernel="auto", counts=None, stream=None):

@@ -22,13 +22,15 @@ constexpr int NCLASSES = 21;  // floor(log4(bytes)) for bytes < 2^42
 std::mutex g_mutex;
 DeviceState g_state[MAX_DEVICES];
 std::unordered_map<cudaStream_t, int> g_slots[MAX_DEVICES];
-pospopcnt_config g_cfg[MAX_DEVICES][3][NCLASSES];
+pospopcnt_config g_cfg[MAX_DEVICES][4][NCLASSES];
 bool g_cfg_ready[MAX_DEVICES] = {};
 std::mutex g_host_mutex[MAX_DEVICES];
 std::atomic<uint64_t> g_launches{0};
 thread_local int t_last_cuda = 0;
 
-int width_index(int width) { return width == 8 ? 0 : width == 16 ? 1 : width == 32 ? 2 : -1; }
+int width_index(int width) {
+  return width == 8 ? 0 : width == 16 ? 1 : width == 32 ? 2 : width == 64 ? 3 : -1;
+}
 
 int size_class(uint64_t bytes) {
   int c = 0;
@@ -56,6 +58,10 @@ pospopcnt_config default_config() {
 // cheapest, and the register path measured fastest at 1-4 GiB).
 pospopcnt_config tuned_default(int width, int cls) {
   pospopcnt_config c = default_config();
+  if (width == 64) {  // one CSA kernel with two circuits per thread
+    c.threads = 256, c.unroll = cls <= 11 ? 4 : 8;
+    return c;
+  }
   if (cls <= 8) {
     c.threads = 512, c.unroll = 8;
     return c;
@@ -81,8 +87,8 @@ pospopcnt_config tuned_default(int width, int cls) {
 
 void init_configs(int dev) {
   if (g_cfg_ready[dev]) return;
-  const int widths[3] = {8, 16, 32};
-  for (int w = 0; w < 3; ++w)
+  const int widths[4] = {8, 16, 32, 64};
+  for (int w = 0; w < 4; ++w)
     for (int c = 0; c < NCLASSES; ++c) g_cfg[dev][w][c] = tuned_default(widths[w], c);
   g_cfg_ready[dev] = true;
 }
@@ -167,6 +173,13 @@ int normalize_config(const DeviceState& st, int width, pospopcnt_config* c) {
   if (c->kernel == POSPOPCNT_KERNEL_AUTO) c->kernel = d.kernel;
   if (c->threads == 0) c->threads = 256;
   if (c->blocks_per_sm < 0 || c->blocks_per_sm > 32) return POSPOPCNT_ERR_INVALID;
+  if (width == 64) {  // 64-bit words: the CSA family, 128 or 256 threads, unroll 4 or 8
+    if (c->unroll == 0) c->unroll = 8;
+    if (c->kernel != POSPOPCNT_KERNEL_CSA || (c->threads != 128 && c->threads != 256) ||
+        (c->unroll != 4 && c->unroll != 8))
+      return POSPOPCNT_ERR_INVALID;
+    return POSPOPCNT_OK;
+  }
   switch (c->kernel) {
     case POSPOPCNT_KERNEL_CSA:
       if (c->unroll == 0) c->unroll = 4;
@@ -203,6 +216,7 @@ int launch_plain(const DeviceState& st, int width, const pospopcnt_config& cfg, 
     case 8: return launch_plain_k<8>(st, cfg, d_in, n, d_counts, zero_first, stream);
     case 16: return launch_plain_k<16>(st, cfg, d_in, n, d_counts, zero_first, stream);
     case 32: return launch_plain_k<32>(st, cfg, d_in, n, d_counts, zero_first, stream);
+    case 64: return launch_plain_k<64>(st, cfg, d_in, n, d_counts, zero_first, stream);
   }
   return POSPOPCNT_ERR_INVALID;
 }
@@ -286,6 +300,9 @@ int pospopcnt_u16(const void* d_in, size_t n, uint64_t* d_counts, cudaStream_t s
 int pospopcnt_u32(const void* d_in, size_t n, uint64_t* d_counts, cudaStream_t stream) {
   return count_impl(32, nullptr, true, d_in, n, d_counts, stream);
 }
+int pospopcnt_u64(const void* d_in, size_t n, uint64_t* d_counts, cudaStream_t stream) {
+  return count_impl(64, nullptr, true, d_in, n, d_counts, stream);
+}
 
 int pospopcnt_count(int width, int kernel, const void* d_in, size_t n, uint64_t* d_counts,
                     cudaStream_t stream) {
@@ -293,7 +310,7 @@ int pospopcnt_count(int width, int kernel, const void* d_in, size_t n, uint64_t*
   if (kernel < 0 || kernel > POSPOPCNT_KERNEL_BALLOT) return POSPOPCNT_ERR_INVALID;
   pospopcnt_config cfg = default_config();
   cfg.kernel = kernel;
-  cfg.unroll = kernel == POSPOPCNT_KERNEL_BALLOT ? 2 : 4;
+  cfg.unroll = kernel == POSPOPCNT_KERNEL_BALLOT ? 2 : width == 64 ? 8 : 4;
   return count_impl(width, &cfg, true, d_in, n, d_counts, stream);
 }
 
@@ -330,7 +347,7 @@ int pospopcnt_count_host(int width, const void* h_in, size_t n, uint64_t* h_coun
   cudaStream_t s0 = st->hstream[0], s1 = st->hstream[1];
   const size_t wb = size_t(width / 8);
   // pinned, mapped host memory: the kernel reads it in place across C2C
-  if (const void* dview = mapped_device_view(h_in, n * wb)) {
+  if (const void* dview = width != 64 ? mapped_device_view(h_in, n * wb) : nullptr) {
     if ((e = cudaMemsetAsync(st->d_acc, 0, sizeof(uint64_t) * size_t(width), s0)) != cudaSuccess)
       return cuda_fail(e);
     if ((rc = launch_plain_sysmem(*st, width, dview, n, st->d_acc, s0)) != POSPOPCNT_OK) return rc;
@@ -374,7 +391,7 @@ int pospopcnt_host_is_mapped(const void* h_in, size_t nbytes) {
 
 int pospopcnt_batched(const void* d_in, const int64_t* d_offsets, size_t nseg, int width, uint64_t* d_counts,
                       cudaStream_t stream) {
-  if (width_index(width) < 0) return POSPOPCNT_ERR_INVALID;
+  if (width != 8 && width != 16 && width != 32) return POSPOPCNT_ERR_INVALID;
   if (nseg == 0) return POSPOPCNT_OK;
   if (!d_in || !d_offsets || !d_counts) return POSPOPCNT_ERR_INVALID;
   if (reinterpret_cast<uintptr_t>(d_in) % uintptr_t(width / 8) != 0) return POSPOPCNT_ERR_MISALIGNED;
@@ -482,7 +499,7 @@ int pospopcnt_autotune(int width, const void* d_in, size_t n, uint64_t* d_scratc
     for (int u : {2, 4, 8}) {
       pospopcnt_config c = default_config();
       c.kernel = POSPOPCNT_KERNEL_CSA, c.threads = t, c.unroll = u;
-      cands.push_back(c);
+      if (normalize_config(*st, width, &c) == POSPOPCNT_OK) cands.push_back(c);
     }
   for (int s : {2, 3, 4, 6, 8})
     for (int ch : {16384, 32768, 65536}) {

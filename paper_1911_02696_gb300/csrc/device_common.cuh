@@ -110,6 +110,13 @@ __device__ __forceinline__ uint32_t load_word(const uint8_t* p) {
   return *reinterpret_cast<const uint32_t*>(p);
 }
 
+// One 64-bit word counted bit by bit into two 32-position halves.
+__device__ __forceinline__ void count_word64(uint32_t (&lo)[32], uint32_t (&hi)[32], const uint8_t* p) {
+  const uint64_t w = *reinterpret_cast<const uint64_t*>(p);
+  count_word<32>(lo, uint32_t(w));
+  count_word<32>(hi, uint32_t(w >> 32));
+}
+
 // ---- streaming 16-byte load ------------------------------------------------
 // Read-only, no L1 allocation, 256-byte L2 prefetch: every input byte is
 // read exactly once.

@@ -248,6 +248,46 @@ __global__ void __launch_bounds__(NTHREADS) ballot_kernel(PlainArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// 64-bit words (wider words as two 32-bit streams, §4): in a 16-byte vector
+// of two words the registers x, z hold positions 0..31 and y, w hold
+// positions 32..63, so each thread runs one carry-save circuit per class
+// (F_L over 2U registers each) and flushes each like a 32-bit stream.
+template <int U, int NTHREADS>
+__global__ void __launch_bounds__(NTHREADS) csa64_kernel(PlainArgs a) {
+  constexpr int H = 2 * U;  // registers per class per trip
+  constexpr int L = ilog2<H>::value;
+  uint32_t Blo[L], Bhi[L];
+#pragma unroll
+  for (int l = 0; l < L; ++l) Blo[l] = 0, Bhi[l] = 0;
+  uint32_t tlo[32], thi[32];
+#pragma unroll
+  for (int p = 0; p < 32; ++p) tlo[p] = 0, thi[p] = 0;
+  const uint64_t stride = uint64_t(gridDim.x) * NTHREADS;
+  uint64_t v = uint64_t(blockIdx.x) * NTHREADS + threadIdx.x;
+  for (; v < a.nvec; v += U * stride) {  // every trip predicated: U loads, missing ones zero
+    uint32_t dlo[H], dhi[H];
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+      const uint64_t idx = v + i * stride;
+      const uint4 x = idx < a.nvec ? ld_stream(a.body + idx) : make_uint4(0, 0, 0, 0);
+      dlo[2 * i] = x.x, dhi[2 * i] = x.y, dlo[2 * i + 1] = x.z, dhi[2 * i + 1] = x.w;
+    }
+    flush<32>(tlo, Circuit<L>::run(dlo, Blo));
+    flush<32>(thi, Circuit<L>::run(dhi, Bhi));
+  }
+  uint32_t clo[32], chi[32];
+  finalize<32, L>(clo, tlo, Blo);
+  finalize<32, L>(chi, thi, Bhi);
+  if (blockIdx.x == 0) {  // head and tail words (at most one each: 8-byte words, 16-byte vectors)
+    if (threadIdx.x < a.head_words) count_word64(clo, chi, a.head + threadIdx.x * 8);
+    if (threadIdx.x >= 32 && threadIdx.x - 32 < a.tail_words) count_word64(clo, chi, a.tail + (threadIdx.x - 32) * 8);
+  }
+  block_reduce_add<32, NTHREADS / 32>(clo, a.counts, a.store != 0);
+  __syncthreads();  // the reduction's shared buffer is reused
+  block_reduce_add<32, NTHREADS / 32>(chi, a.counts + 32, a.store != 0);
+}
+
+// ---------------------------------------------------------------------------
 // Host launcher for width K.
 
 template <typename Kern>
@@ -368,6 +408,21 @@ int launch_plain_sysmem_k(const DeviceState& st, const void* d_in, size_t n, uns
   return launch_csa<K, 4, 256, true>(st, a, 0, false, stream);
 }
 
+template <int U, int T>
+static int launch_csa64(const DeviceState& st, PlainArgs a, int bps, bool zero_first, cudaStream_t stream) {
+  auto kern = csa64_kernel<U, T>;
+  const int occ = occupancy(kern, T, 0);
+  const uint64_t cap = uint64_t(st.sms) * uint64_t(std::min(bps > 0 ? bps : occ, occ));
+  const uint64_t need = (a.nvec + uint64_t(U) * T - 1) / (uint64_t(U) * T);
+  uint64_t grid = std::max<uint64_t>(1, std::min(cap, need));
+  grid = std::max(grid, min_blocks_for(a.nvec * 16));
+  if (const int rc = prepare_counts<64>(a, grid, zero_first, stream)) return rc;
+  kern<<<unsigned(grid), T, 0, stream>>>(a);
+  note_launch();
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? POSPOPCNT_OK : cuda_fail(e);
+}
+
 template <int K>
 int launch_plain_k(const DeviceState& st, const pospopcnt_config& cfg, const void* d_in, size_t n,
                    unsigned long long* d_counts, bool zero_first, cudaStream_t stream) {
@@ -388,6 +443,15 @@ int launch_plain_k(const DeviceState& st, const pospopcnt_config& cfg, const voi
     const cudaError_t e = cudaMemsetAsync(d_counts, 0, sizeof(unsigned long long) * K, stream);
     return e == cudaSuccess ? POSPOPCNT_OK : cuda_fail(e);
   }
+  if constexpr (K == 64) {  // one kernel family for 64-bit words
+    switch (cfg.threads) {
+      case 128: return cfg.unroll == 8 ? launch_csa64<8, 128>(st, a, cfg.blocks_per_sm, zero_first, stream)
+                                       : launch_csa64<4, 128>(st, a, cfg.blocks_per_sm, zero_first, stream);
+      case 256: return cfg.unroll == 8 ? launch_csa64<8, 256>(st, a, cfg.blocks_per_sm, zero_first, stream)
+                                       : launch_csa64<4, 256>(st, a, cfg.blocks_per_sm, zero_first, stream);
+    }
+    return POSPOPCNT_ERR_INVALID;
+  } else {
   switch (cfg.kernel) {
     case POSPOPCNT_KERNEL_CSA:
       switch (cfg.threads) {
@@ -408,6 +472,7 @@ int launch_plain_k(const DeviceState& st, const pospopcnt_config& cfg, const voi
       return POSPOPCNT_ERR_INVALID;
   }
   return POSPOPCNT_ERR_INVALID;
+  }
 }
 
 }  // namespace ppc

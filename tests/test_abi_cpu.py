@@ -106,10 +106,13 @@ def test_argument_checks_need_no_device():
     assert lib.pospopcnt_count_accumulate(7, good, 5, good, None) == 1
     # too large
     assert lib.pospopcnt_u8(good, 1 << 43, good, None) == 6
+    # 64-bit words: 8-byte alignment; only the CSA family
+    assert lib.pospopcnt_u64(P((1 << 20) + 4), 5, good, None) == 2
     # batched: nseg == 0 is a no-op; null pointers; bad width; misalignment
     assert lib.pospopcnt_batched(None, None, 0, 16, None, None) == 0
     assert lib.pospopcnt_batched(good, None, 3, 16, good, None) == 1
     assert lib.pospopcnt_batched(good, good, 3, 24, good, None) == 1
+    assert lib.pospopcnt_batched(good, good, 3, 64, good, None) == 1
     assert lib.pospopcnt_batched(P((1 << 20) + 1), good, 3, 16, good, None) == 2
     assert lib.pospopcnt_batched(good, P((1 << 20) + 4), 3, 16, good, None) == 2
     # host path

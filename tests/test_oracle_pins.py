@@ -120,7 +120,7 @@ def pin_popcount_total(count):
 def pin_unpackbits(count):
     """Brute force: the 'vertical' column sums of the bit matrix (§1, Fig. 1)
     taken with numpy.unpackbits on the little-endian bytes."""
-    for k in WIDTHS:
+    for k in WIDTHS + (64,):
         for seed, n in ((10, 1), (11, 31), (12, 1000), (13, 4096)):
             w = synth.uniform_bits(seed, n, k)
             bits = np.unpackbits(w.view(np.uint8), bitorder="little").reshape(n, k)
@@ -130,11 +130,14 @@ def pin_unpackbits(count):
 
 def pin_cross_width(count):
     """Wider words are narrower streams side by side (§4): over the same
-    little-endian bytes c8[p] = c16[p] + c16[p+8] and c16[p] = c32[p] + c32[p+16]."""
-    b = synth.uniform_bytes(21, 4096 * 4)
+    little-endian bytes c8[p] = c16[p] + c16[p+8], c16[p] = c32[p] + c32[p+16]
+    and c32[p] = c64[p] + c64[p+32]."""
+    b = synth.uniform_bytes(21, 4096 * 8)
     c8, c16, c32 = count(b, 8), count(b.view(np.uint16), 16), count(b.view(np.uint32), 32)
+    c64 = count(b.view(np.uint64), 64)
     assert np.array_equal(c8, c16[:8] + c16[8:])
     assert np.array_equal(c16, c32[:16] + c32[16:])
+    assert np.array_equal(c32, c64[:32] + c64[32:])
 
 
 def pin_complement(count):

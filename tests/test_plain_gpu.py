@@ -264,3 +264,44 @@ def test_overwrite_across_grid_sizes(width):
         run_kernel(width, None, x, out)
         torch.cuda.synchronize()
         assert np.array_equal(_as_u64(out), oracle.pospopcnt(words, width)), nbytes
+
+
+def test_u64_every_small_length_and_alignment():
+    """64-bit words: n = 0..299 at both 8-byte alignments within 16 bytes."""
+    words = synth.uniform_bits(64, 300, 64)
+    for offset in (0, 8):
+        _, x_all = _device_slice(words, offset)
+        full = torch.full((300, 72), SENTINEL, dtype=torch.int64, device="cuda")
+        for n in range(300):
+            ppc.pospopcnt_u64(x_all[: n * 8], counts=full[n, :64])
+        torch.cuda.synchronize()
+        got = full.cpu().numpy()
+        for n in range(300):
+            assert np.array_equal(got[n, :64].view(np.uint64), oracle.pospopcnt(words[:n], 64)), (offset, n)
+            assert np.all(got[n, 64:] == SENTINEL)
+
+
+def test_u64_configs_and_sizes():
+    rng = np.random.default_rng(640)
+    for cfg in (None, dict(kernel="csa", threads=128, unroll=4), dict(kernel="csa", threads=256, unroll=8)):
+        for _ in range(3):
+            n = int(rng.integers(1, 6 << 20))
+            words = synth.uniform_bits(int(rng.integers(1 << 30)), n, 64)
+            _, x = _device_slice(words, 8 * int(rng.integers(0, 2)))
+            out = torch.full((64,), -3, dtype=torch.int64, device="cuda")
+            if cfg is None:
+                ppc.pospopcnt_u64(x, counts=out)
+            else:
+                ppc.pospopcnt_count_config(64, cfg, x, counts=out)
+            torch.cuda.synchronize()
+            assert np.array_equal(_as_u64(out), oracle.pospopcnt(words, 64))
+    with pytest.raises(ppc.PospopcntError):
+        ppc.pospopcnt_count(64, torch.zeros(64, dtype=torch.uint8, device="cuda"), "tma")
+
+
+@pytest.mark.slow
+def test_full_u64():
+    """2^28 64-bit words (2 GiB): uniform bits and one-hot over 64 positions."""
+    _full(64, synth.uniform_bits(2, 1 << 28, 64), kernels=("auto",))
+    ref = _full(64, synth.one_hot(2, 1 << 28, 64, cdf=synth.uniform_cdf(64)), kernels=("auto",))
+    assert int(ref.sum()) == 1 << 28
