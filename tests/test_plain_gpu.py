@@ -46,7 +46,7 @@ def run_kernel(width, kernel, x, out, cfg=None):
     if cfg is not None:
         return ppc.pospopcnt_count_config(width, cfg, x, counts=out)
     if kernel is None:
-        return {8: ppc.pospopcnt_u8, 16: ppc.pospopcnt_u16, 32: ppc.pospopcnt_u32}[width](x, counts=out)
+        return {8: ppc.pospopcnt_u8, 16: ppc.pospopcnt_u16, 32: ppc.pospopcnt_u32, 64: ppc.pospopcnt_u64}[width](x, counts=out)
     return ppc.pospopcnt_count(width, x, kernel, counts=out)
 
 
