@@ -93,7 +93,7 @@ int pospopcnt_u32(const void* d_in, size_t n, uint64_t* d_counts, cudaStream_t s
  * are narrower streams side by side (§4): in each 16-byte vector the 32-bit
  * registers alternate between positions 0..31 and 32..63, and each thread
  * runs one carry-save circuit per class.  pospopcnt_count / _config /
- * _accumulate / _count_host also take width 64 (CSA kernel family only);
+ * _accumulate / _count_host also take width 64 (CSA and TMA families);
  * the batched and serving forms take 8, 16 or 32. */
 int pospopcnt_u64(const void* d_in, size_t n, uint64_t* d_counts, cudaStream_t stream);
 

@@ -58,7 +58,11 @@ pospopcnt_config default_config() {
 // cheapest, and the register path measured fastest at 1-4 GiB).
 pospopcnt_config tuned_default(int width, int cls) {
   pospopcnt_config c = default_config();
-  if (width == 64) {  // one CSA kernel with two circuits per thread
+  if (width == 64) {  // two circuits per thread; the bulk-copy ring from 64 MiB
+    if (cls >= 13) {
+      c.kernel = POSPOPCNT_KERNEL_TMA, c.stages = 3, c.chunk_bytes = 65536;
+      return c;
+    }
     c.threads = 256, c.unroll = cls <= 11 ? 4 : 8;
     return c;
   }
@@ -173,7 +177,7 @@ int normalize_config(const DeviceState& st, int width, pospopcnt_config* c) {
   if (c->kernel == POSPOPCNT_KERNEL_AUTO) c->kernel = d.kernel;
   if (c->threads == 0) c->threads = 256;
   if (c->blocks_per_sm < 0 || c->blocks_per_sm > 32) return POSPOPCNT_ERR_INVALID;
-  if (width == 64) {  // 64-bit words: the CSA family, 128 or 256 threads, unroll 4 or 8
+  if (width == 64 && c->kernel != POSPOPCNT_KERNEL_TMA) {  // 64-bit words: CSA 128/256 threads, unroll 4/8
     if (c->unroll == 0) c->unroll = 8;
     if (c->kernel != POSPOPCNT_KERNEL_CSA || (c->threads != 128 && c->threads != 256) ||
         (c->unroll != 4 && c->unroll != 8))

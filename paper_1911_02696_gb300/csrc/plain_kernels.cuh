@@ -105,8 +105,22 @@ struct TmaArgs {
   uint32_t stages;
 };
 
+// Register classes of the TMA consumers: for K <= 32 every 32-bit register
+// of a vector holds all K positions; for 64-bit words registers alternate
+// between positions 0..31 (x, z) and 32..63 (y, w), one circuit per class.
+template <int K>
+struct tma_shape {
+  static constexpr int NC = K == 64 ? 2 : 1;        // register classes
+  static constexpr int KC = K == 64 ? 32 : K;       // positions per class
+  static constexpr int VPT = K == 64 ? 8 : 4;       // 16-byte vectors per thread per trip
+  static constexpr int RC = 4 * VPT / NC;           // registers per class per trip
+  static constexpr int L = ilog2<RC>::value;        // circuit depth per class
+};
+
 template <int K>
 __global__ void __launch_bounds__(TMA_THREADS) tma_kernel(TmaArgs a) {
+  using S = tma_shape<K>;
+  constexpr int NC = S::NC, KC = S::KC, VPT = S::VPT, RC = S::RC, L = S::L;
   extern __shared__ __align__(128) uint8_t ring[];
   __shared__ __align__(8) uint64_t full[TMA_MAX_STAGES];
   __shared__ __align__(8) uint64_t empty[TMA_MAX_STAGES];
@@ -115,13 +129,13 @@ __global__ void __launch_bounds__(TMA_THREADS) tma_kernel(TmaArgs a) {
   __shared__ uint32_t s_abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t S = a.stages;
+  const uint32_t S_ = a.stages;
   const uint64_t nchunks = (a.body_bytes + a.chunk_bytes - 1) / a.chunk_bytes;
   const uint32_t my_chunks =
       blockIdx.x < nchunks ? uint32_t((nchunks - 1 - blockIdx.x) / gridDim.x + 1) : 0u;
 
   if (threadIdx.x == 0) {
-    for (uint32_t s = 0; s < S; ++s) {
+    for (uint32_t s = 0; s < S_; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], TMA_CWARPS);
     }
@@ -131,16 +145,18 @@ __global__ void __launch_bounds__(TMA_THREADS) tma_kernel(TmaArgs a) {
   }
   __syncthreads();
 
-  uint32_t c[K];
+  uint32_t c[NC][KC];
 #pragma unroll
-  for (int p = 0; p < K; ++p) c[p] = 0;
+  for (int q = 0; q < NC; ++q)
+#pragma unroll
+    for (int p = 0; p < KC; ++p) c[q][p] = 0;
 
   if (warp == TMA_CWARPS) {
     // producer: one lane issues every copy
     if (lane == 0) {
       uint32_t i = 0;
       for (; i < my_chunks; ++i) {
-        const uint32_t s = i % S, use = i / S;
+        const uint32_t s = i % S_, use = i / S_;
         if (use > 0 && !mbar_wait_bounded(&empty[s], (use - 1) & 1u, WAIT_LIMIT_NS)) {
           atomicOr(a.p.err, ERR_BIT_TIMEOUT_EMPTY);
           atomicExch(&s_abort, 1u);
@@ -159,13 +175,18 @@ __global__ void __launch_bounds__(TMA_THREADS) tma_kernel(TmaArgs a) {
   } else {
     // consumers
     constexpr int CT = TMA_CWARPS * 32;
-    uint32_t B[4] = {0, 0, 0, 0};
-    uint32_t top[K];
+    uint32_t B[NC][L];
+    uint32_t top[NC][KC];
 #pragma unroll
-    for (int p = 0; p < K; ++p) top[p] = 0;
+    for (int q = 0; q < NC; ++q) {
+#pragma unroll
+      for (int l = 0; l < L; ++l) B[q][l] = 0;
+#pragma unroll
+      for (int p = 0; p < KC; ++p) top[q][p] = 0;
+    }
     uint32_t i = 0;
     for (; i < my_chunks; ++i) {
-      const uint32_t s = i % S, use = i / S;
+      const uint32_t s = i % S_, use = i / S_;
       // every lane waits (each acquires the copied bytes); the verdict is
       // made warp-uniform so the warp leaves the loop together
       const bool ok = __all_sync(FULL_MASK, mbar_wait_bounded(&full[s], use & 1u, WAIT_LIMIT_NS));
@@ -181,15 +202,18 @@ __global__ void __launch_bounds__(TMA_THREADS) tma_kernel(TmaArgs a) {
       const uint64_t rem = a.body_bytes - off;
       const uint32_t nv = (rem < a.chunk_bytes ? uint32_t(rem) : a.chunk_bytes) / 16u;
       const uint4* sv = reinterpret_cast<const uint4*>(ring + size_t(s) * a.chunk_bytes);
-      for (uint32_t base = 0; base < nv; base += 4 * CT) {
-        uint32_t d[16];
+      for (uint32_t base = 0; base < nv; base += VPT * CT) {
+        uint32_t d[NC][RC];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < VPT; ++j) {
           const uint32_t idx = base + j * CT + threadIdx.x;
           const uint4 x = idx < nv ? sv[idx] : make_uint4(0, 0, 0, 0);
-          d[4 * j + 0] = x.x, d[4 * j + 1] = x.y, d[4 * j + 2] = x.z, d[4 * j + 3] = x.w;
+          const uint32_t r[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) d[q % NC][(4 * j + q) / NC] = r[q];
         }
-        flush<K>(top, Circuit<4>::run(d, B));
+#pragma unroll
+        for (int q = 0; q < NC; ++q) flush<KC>(top[q], Circuit<L>::run(d[q], B[q]));
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);
@@ -199,7 +223,8 @@ __global__ void __launch_bounds__(TMA_THREADS) tma_kernel(TmaArgs a) {
       }
     }
     if (lane == 0) s_consumed[warp] = i;
-    finalize<K, 4>(c, top, B);
+#pragma unroll
+    for (int q = 0; q < NC; ++q) finalize<KC, L>(c[q], top[q], B[q]);
   }
   __syncthreads();
   // After an abort, wait (bounded) for copies still in flight before the
@@ -208,14 +233,26 @@ __global__ void __launch_bounds__(TMA_THREADS) tma_kernel(TmaArgs a) {
     uint32_t lo = s_issued;
     for (int w = 0; w < TMA_CWARPS; ++w) lo = s_consumed[w] < lo ? s_consumed[w] : lo;
     for (uint32_t i = lo; i < s_issued; ++i) {
-      if (!mbar_wait_bounded(&full[i % S], (i / S) & 1u, WAIT_LIMIT_NS)) {
+      if (!mbar_wait_bounded(&full[i % S_], (i / S_) & 1u, WAIT_LIMIT_NS)) {
         atomicOr(a.p.err, ERR_BIT_TIMEOUT_DRAIN);
         break;
       }
     }
   }
-  count_head_tail<K, TMA_THREADS>(c, a.p);
-  block_reduce_add<K, TMA_CWARPS + 1>(c, a.p.counts, a.p.store != 0);
+  if constexpr (K == 64) {
+    if (blockIdx.x == 0) {
+      if (threadIdx.x < a.p.head_words) count_word64(c[0], c[1], a.p.head + threadIdx.x * 8);
+      if (threadIdx.x >= 32 && threadIdx.x - 32 < a.p.tail_words)
+        count_word64(c[0], c[1], a.p.tail + (threadIdx.x - 32) * 8);
+    }
+  } else {
+    count_head_tail<K, TMA_THREADS>(c[0], a.p);
+  }
+#pragma unroll
+  for (int q = 0; q < NC; ++q) {
+    if (q) __syncthreads();  // the reduction's shared buffer is reused
+    block_reduce_add<KC, TMA_CWARPS + 1>(c[q], a.p.counts + 32 * q, a.p.store != 0);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -443,7 +480,11 @@ int launch_plain_k(const DeviceState& st, const pospopcnt_config& cfg, const voi
     const cudaError_t e = cudaMemsetAsync(d_counts, 0, sizeof(unsigned long long) * K, stream);
     return e == cudaSuccess ? POSPOPCNT_OK : cuda_fail(e);
   }
-  if constexpr (K == 64) {  // one kernel family for 64-bit words
+  if constexpr (K == 64) {  // 64-bit words: the CSA and TMA families
+    if (cfg.kernel == POSPOPCNT_KERNEL_TMA) {
+      if (a.nvec == 0) return launch_csa64<4, 256>(st, a, 1, zero_first, stream);  // head/tail only
+      return launch_tma<K>(st, a, cfg.blocks_per_sm, cfg.stages, cfg.chunk_bytes, zero_first, stream);
+    }
     switch (cfg.threads) {
       case 128: return cfg.unroll == 8 ? launch_csa64<8, 128>(st, a, cfg.blocks_per_sm, zero_first, stream)
                                        : launch_csa64<4, 128>(st, a, cfg.blocks_per_sm, zero_first, stream);

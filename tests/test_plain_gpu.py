@@ -283,7 +283,8 @@ def test_u64_every_small_length_and_alignment():
 
 def test_u64_configs_and_sizes():
     rng = np.random.default_rng(640)
-    for cfg in (None, dict(kernel="csa", threads=128, unroll=4), dict(kernel="csa", threads=256, unroll=8)):
+    for cfg in (None, dict(kernel="csa", threads=128, unroll=4), dict(kernel="csa", threads=256, unroll=8),
+                dict(kernel="tma", stages=3, chunk_bytes=65536), dict(kernel="tma", stages=4, chunk_bytes=16384)):
         for _ in range(3):
             n = int(rng.integers(1, 6 << 20))
             words = synth.uniform_bits(int(rng.integers(1 << 30)), n, 64)
@@ -296,12 +297,12 @@ def test_u64_configs_and_sizes():
             torch.cuda.synchronize()
             assert np.array_equal(_as_u64(out), oracle.pospopcnt(words, 64))
     with pytest.raises(ppc.PospopcntError):
-        ppc.pospopcnt_count(64, torch.zeros(64, dtype=torch.uint8, device="cuda"), "tma")
+        ppc.pospopcnt_count(64, torch.zeros(64, dtype=torch.uint8, device="cuda"), "ballot")
 
 
 @pytest.mark.slow
 def test_full_u64():
     """2^28 64-bit words (2 GiB): uniform bits and one-hot over 64 positions."""
-    _full(64, synth.uniform_bits(2, 1 << 28, 64), kernels=("auto",))
+    _full(64, synth.uniform_bits(2, 1 << 28, 64), kernels=("auto", "csa", "tma"))
     ref = _full(64, synth.one_hot(2, 1 << 28, 64, cdf=synth.uniform_cdf(64)), kernels=("auto",))
     assert int(ref.sum()) == 1 << 28
