@@ -208,6 +208,11 @@ def make_input(kind: str, seed: int, log2_words: int | None = None):
                 "pospopcnt_u16 n=2^30+7 uniform bits, start 2 bytes past a 256-byte boundary")
     if kind == "u8":
         return synth.uniform_bits(seed, 1 << 31, 8), 8, 0, "pospopcnt_u8 n=2^31 uniform random bits (2 GiB)"
+    if kind == "onehot":
+        ids = synth.categorical_ids(seed, 1 << 31, synth.zipf_cdf(16), np.uint8)
+        return ids, -16, 0, "fused one-hot encode + count: 2^31 u8 ids, Zipf(1.1) over 16 categories (2 GiB)"
+    if kind == "popcount":
+        return synth.uniform_bytes(seed, 1 << 31), 1, 0, "array popcount of 2 GiB of uniform random bits"
     if kind == "u64":
         return synth.uniform_bits(seed, 1 << 28, 64), 64, 0, "pospopcnt_u64 n=2^28 uniform random bits (2 GiB)"
     if kind == "u32":
@@ -240,20 +245,27 @@ def run_plain(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     words, width, offset, desc = make_input(args.workload, seed=rank, log2_words=args.log2_words)
-    nbytes = words.size * (width // 8)
+    nbytes = words.nbytes  # width 1 is the array popcount over bytes
     host = torch.from_numpy(words.view(np.uint8))
     buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
     x = buf[offset: offset + nbytes]
     x.copy_(host)
-    counts = torch.empty(width, dtype=torch.int64, device=dev)
+    onehot_k = -width if width < 0 else 0  # negative width marks the one-hot workload (k categories)
+    if onehot_k:
+        width = 1
+    counts = torch.empty(onehot_k or width, dtype=torch.int64, device=dev)
     ppc.pospopcnt_init(local)
-    if args.kernel:  # a named kernel family in its default configuration (comparison / profiling)
+    if onehot_k:
+        def fn(t, counts):
+            return ppc.pospopcnt_onehot_counts(t, onehot_k, counts=counts)
+    elif args.kernel:  # a named kernel family in its default configuration (comparison / profiling)
         fixed = {"kernel": args.kernel}
 
         def fn(t, counts):
             return ppc.pospopcnt_count_config(width, fixed, t, counts=counts)
     else:
-        fn = {8: ppc.pospopcnt_u8, 16: ppc.pospopcnt_u16, 32: ppc.pospopcnt_u32, 64: ppc.pospopcnt_u64}[width]
+        fn = {8: ppc.pospopcnt_u8, 16: ppc.pospopcnt_u16, 32: ppc.pospopcnt_u32, 64: ppc.pospopcnt_u64,
+          1: lambda t, counts: ppc.pospopcnt_popcount(t, count=counts)}[width]
     stream = torch.cuda.current_stream(dev)
 
     # correctness of the timed configuration (oracle on rank 0's host copy is
@@ -288,7 +300,7 @@ def run_plain(args, world, rank, local):
 
     # end to end through the host-buffer entry point
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not onehot_k and width != 1:
         pinned = host.pin_memory()
         ppc.pospopcnt_count_host(width, pinned)  # allocates staging once
         k_e2e = max(1, min(args.steps, args.e2e_steps))
@@ -303,10 +315,12 @@ def run_plain(args, world, rank, local):
     peak, peak_src = peak_hbm()
     launch_ms = statistics.mean(per_step)
     achieved = (nbytes + width * 8) / (launch_ms * 1e-3) / 1e9
-    cfg = ppc.pospopcnt_get_config(width, words.size)
+    cfg = ppc.pospopcnt_get_config(16 if width == 1 else width, words.size // (2 if width == 1 else 1))
     if args.kernel:
         cfg = {"kernel": ppc.KERNELS[args.kernel], "note": "library default launch for this family"}
     kname = {1: "csa", 2: "tma", 3: "ballot"}[cfg["kernel"]]
+    if onehot_k:
+        cfg, kname = {"kernel": "onehot", "k": onehot_k}, "onehot"
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_source": f"{peak_src} (copy bandwidth)",
                 "traffic": profiled_traffic(f"{kname}_u{width}", nbytes),
@@ -314,23 +328,26 @@ def run_plain(args, world, rank, local):
     out = None
     if rank == 0:
         out = {
-            "metric": METRIC if width == 16 else f"pospopcnt_u{width} GB/s", "value": round(value, 2),
+            "metric": METRIC if width == 16 else ("onehot_counts GB/s" if onehot_k else
+                                                  "popcount GB/s" if width == 1 else f"pospopcnt_u{width} GB/s"),
+            "value": round(value, 2),
             "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(max_ms / args.steps, 5), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": f"u{width}", "data": "synthetic (seeded SplitMix64 on the host)",
+            "vs_baseline": None, "dtype": "u8" if width == 1 else f"u{width}",
+            "data": "synthetic (seeded SplitMix64 on the host)",
             "config": {"workload": desc, "n_words": int(words.size), "width": width, "start_offset_bytes": offset,
                        "bytes_per_rank_step": nbytes, "launch_config": cfg, "parallelism": f"replicas x{world}",
                        "l2": f"input {nbytes / 2**20:.0f} MiB vs L2 126 MB: "
                              + ("no flush needed" if nbytes > (256 << 20) else "L2-resident (profiling case)")},
-            "words_per_s": round(value * 1e9 / (width // 8), 1),
+            "words_per_s": round(value * 1e9 / max(1, width // 8), 1),
             "pct_hbm_peak": round(100 * value / world / peak, 2),
             "roofline": roofline,
             "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clocks.summary(),
         }
-        if not args.no_cpu_baseline and world == 1:
-            out["cpu_baseline"] = cpu_baseline(words, width)
+        if not args.no_cpu_baseline and world == 1 and not onehot_k:
+            out["cpu_baseline"] = cpu_baseline(words, max(width, 8))
     return out
 
 
@@ -702,7 +719,8 @@ def main(argv=None):
     p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="u16",
-                   choices=["u16", "u16_onehot", "u16_sparse", "u16_misaligned", "u8", "u32", "u64", "sweep", "batched",
+                   choices=["u16", "u16_onehot", "u16_sparse", "u16_misaligned", "u8", "u32", "u64", "popcount", "onehot",
+                            "sweep", "batched",
                             "kernels", "autotune", "serve", "e2e"])
     p.add_argument("--batched-nseg", type=int, default=20000)
     p.add_argument("--serve-rate", type=float, default=50000.0)

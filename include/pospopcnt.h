@@ -97,6 +97,24 @@ int pospopcnt_u32(const void* d_in, size_t n, uint64_t* d_counts, cudaStream_t s
  * the batched and serving forms take 8, 16 or 32. */
 int pospopcnt_u64(const void* d_in, size_t n, uint64_t* d_counts, cudaStream_t stream);
 
+/* Array popcount: the number of set bits in nbytes bytes at d_in, written
+ * to *d_count (device memory, one uint64).  This is the single sum that the
+ * positional count generalises (Abstract; the Harley-Seal popcount of §2):
+ * the same carry-save circuit with one counter, whose flush is one popc of
+ * the top register.  Any start address; asynchronous on `stream`. */
+int pospopcnt_popcount(const void* d_in, size_t nbytes, uint64_t* d_count, cudaStream_t stream);
+
+/* Fused one-hot encode + count: the frequency histogram of n categorical
+ * ids (unsigned, id_bytes = 1, 2 or 4 bytes each, little-endian, d_ids
+ * aligned to id_bytes) over k categories, 1 <= k <= 32: d_counts[v] = the
+ * number of ids equal to v, for v < k (k uint64 values, overwritten); ids
+ * >= k are not counted.  This is the pipeline that motivates the paper (§1,
+ * Table 1: values one-hot encoded, then positionally counted), with the
+ * one-hot words built in registers and never written to memory.
+ * Asynchronous on `stream`. */
+int pospopcnt_onehot_counts(const void* d_ids, size_t n, int id_bytes, int k, uint64_t* d_counts,
+                            cudaStream_t stream);
+
 /* The same for width 8, 16 or 32 with an explicit kernel family
  * (pospopcnt_kernel). */
 int pospopcnt_count(int width, int kernel, const void* d_in, size_t n, uint64_t* d_counts,

@@ -16,6 +16,10 @@ Functions (each cites the passage it follows in the C source):
   (§2 Fig. 3-4, §3, §4.1), which reaches the definition exactly.
 * ``csa_truth(which)`` / ``csa_circuit_size(N)`` -- Table 2 immediates and
   the 2^N - 1 circuit size of §2.
+* ``popcount(data)`` -- the number of set bits (Abstract, §2): the single sum
+  pospopcnt generalises.
+* ``onehot_counts(ids, k)`` -- one-hot encode then count: the frequency
+  histogram of §1 / Table 1.
 
 Parity pins: tests/test_oracle_pins.py.  No function here is "parity
 unpinned".
@@ -67,6 +71,10 @@ def _load():
             lib.oracle_csa_truth.argtypes = [i32]
             lib.oracle_csa_circuit_size.restype = i64
             lib.oracle_csa_circuit_size.argtypes = [i32]
+            lib.oracle_popcount.restype = i32
+            lib.oracle_popcount.argtypes = [vp, u64, vp]
+            lib.oracle_onehot_counts.restype = i32
+            lib.oracle_onehot_counts.argtypes = [vp, u64, i32, i32, vp]
             _lib = lib
     return _lib
 
@@ -138,6 +146,24 @@ def csa_pospopcnt(words, width: int | None = None, N: int = 4):
                                          out.ctypes.data)
     assert calls >= 0
     return out, int(calls)
+
+
+def popcount(data) -> int:
+    """Number of set bits in the bytes of `data` (bit by bit)."""
+    a = np.ascontiguousarray(data)
+    out = np.zeros(1, dtype=np.uint64)
+    assert _load().oracle_popcount(a.ctypes.data, a.size * a.itemsize, out.ctypes.data) == 0
+    return int(out[0])
+
+
+def onehot_counts(ids, k: int) -> np.ndarray:
+    """Frequency histogram of categorical ids by one-hot encoding then
+    positional counting (§1); ids >= k are not counted.  uint64[k]."""
+    a = np.ascontiguousarray(ids)
+    assert a.dtype in (np.uint8, np.uint16, np.uint32)
+    out = np.zeros(k, dtype=np.uint64)
+    assert _load().oracle_onehot_counts(a.ctypes.data, a.size, a.itemsize, k, out.ctypes.data) == 0
+    return out
 
 
 def csa_truth(which: int) -> int:

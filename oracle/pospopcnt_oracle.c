@@ -22,6 +22,12 @@
  *       baseline on all host cores.
  *   oracle_pospopcnt_segments
  *       One definition per segment [offsets[s], offsets[s+1]).
+ *   oracle_popcount
+ *       The number of set bits of a byte array, bit by bit: the single sum
+ *       that pospopcnt generalises (Abstract, §2).
+ *   oracle_onehot_counts
+ *       Categorical ids one-hot encoded, then positionally counted: the
+ *       frequency histogram that motivates the paper (§1, Table 1).
  *   oracle_csa_*
  *       The paper's own method, step by step in its order: the carry-save
  *       adder (§2, Fig. 3), the recursive Harley-Seal circuit F_N built from
@@ -70,6 +76,38 @@ int oracle_pospopcnt(int k, const void* in, uint64_t n, uint64_t* counts) {
   if (!width_ok(k) || !counts) return -1;
   memset(counts, 0, sizeof(uint64_t) * (size_t)k);
   return oracle_pospopcnt_add(k, in, n, counts);
+}
+
+/* Population count of a byte array (the single sum that pospopcnt
+ * generalises, Abstract and §2): the number of set bits, bit by bit. */
+int oracle_popcount(const void* in, uint64_t nbytes, uint64_t* count) {
+  if ((nbytes && !in) || !count) return -1;
+  const unsigned char* b = (const unsigned char*)in;
+  uint64_t c = 0;
+  for (uint64_t i = 0; i < nbytes; ++i)
+    for (int j = 0; j < 8; ++j) c += (b[i] >> j) & 1u;
+  *count = c;
+  return 0;
+}
+
+/* The pipeline that motivates the paper (§1, Table 1): categorical ids are
+ * one-hot encoded -- id v becomes the word with only bit v set (ids >= k map
+ * to the empty word) -- and the words' positional counts are the frequency
+ * histogram.  Written in that order: encode a word, then count its bits.
+ * ids: n unsigned little-endian integers of id_bytes (1, 2 or 4) bytes;
+ * counts: k values, 1 <= k <= 64. */
+int oracle_onehot_counts(const void* ids, uint64_t n, int id_bytes, int k, uint64_t* counts) {
+  if ((id_bytes != 1 && id_bytes != 2 && id_bytes != 4) || k < 1 || k > 64 || (n && !ids) || !counts)
+    return -1;
+  const unsigned char* b = (const unsigned char*)ids;
+  memset(counts, 0, sizeof(uint64_t) * (size_t)k);
+  for (uint64_t i = 0; i < n; ++i) {
+    uint64_t v = 0;
+    for (int j = 0; j < id_bytes; ++j) v |= (uint64_t)b[i * (uint64_t)id_bytes + (uint64_t)j] << (8 * j);
+    const uint64_t word = v < (uint64_t)k ? (uint64_t)1 << v : 0; /* one-hot encoding */
+    for (int p = 0; p < k; ++p) counts[p] += (word >> p) & 1u;       /* positional count */
+  }
+  return 0;
 }
 
 /* ---- the same definition over contiguous chunks on threads -------------- */

@@ -21,7 +21,7 @@ import numpy as np
 from . import _build
 
 __all__ = [
-    "PospopcntError", "load", "pospopcnt_init", "pospopcnt_u8", "pospopcnt_u16", "pospopcnt_u32", "pospopcnt_u64",
+    "PospopcntError", "load", "pospopcnt_init", "pospopcnt_u8", "pospopcnt_u16", "pospopcnt_u32", "pospopcnt_u64", "pospopcnt_popcount", "pospopcnt_onehot_counts",
     "pospopcnt_count", "pospopcnt_count_config", "pospopcnt_count_accumulate", "pospopcnt_count_host",
     "pospopcnt_host_is_mapped",
     "pospopcnt_batched", "pospopcnt_batched_noalloc", "pospopcnt_plain_segments", "pospopcnt_check_device_error", "pospopcnt_plan_split",
@@ -111,6 +111,8 @@ def _declare(lib):
         "pospopcnt_u16": (i32, [vp, sz, vp, vp]),
         "pospopcnt_u32": (i32, [vp, sz, vp, vp]),
         "pospopcnt_u64": (i32, [vp, sz, vp, vp]),
+        "pospopcnt_popcount": (i32, [vp, sz, vp, vp]),
+        "pospopcnt_onehot_counts": (i32, [vp, sz, i32, i32, vp, vp]),
         "pospopcnt_count": (i32, [i32, i32, vp, sz, vp, vp]),
         "pospopcnt_count_config": (i32, [i32, P(Config), vp, sz, vp, vp]),
         "pospopcnt_count_accumulate": (i32, [i32, vp, sz, vp, vp]),
@@ -217,6 +219,32 @@ def pospopcnt_u32(x, counts=None, stream=None):
 def pospopcnt_u64(x, counts=None, stream=None):
     """Counts of the 64-bit words of CUDA tensor x (int64[64])."""
     return _plain("pospopcnt_u64", 64, x, counts, stream)
+
+
+def pospopcnt_popcount(x, count=None, stream=None):
+    """Number of set bits in the bytes of CUDA tensor x (int64[1])."""
+    torch = _torch()
+    ptr, nbytes = _words(x, 8)
+    out = _counts_out(count, 1, None, x.device)
+    with torch.cuda.device(x.device):
+        _check(_lib().pospopcnt_popcount(ptr, nbytes, out.data_ptr(), _stream_handle(stream, x.device)),
+               "pospopcnt_popcount")
+    return out
+
+
+def pospopcnt_onehot_counts(ids, k: int, counts=None, stream=None):
+    """Histogram of categorical ids (CUDA tensor of uint8/int16/int32 viewed
+    as unsigned ids) over k <= 32 categories; ids >= k are not counted."""
+    torch = _torch()
+    idb = ids.element_size()
+    if idb not in (1, 2, 4):
+        raise ValueError("ids must be 1-, 2- or 4-byte integers")
+    ptr, n = _words(ids, 8 * idb)
+    out = _counts_out(counts, k, None, ids.device)
+    with torch.cuda.device(ids.device):
+        _check(_lib().pospopcnt_onehot_counts(ptr, n, idb, k, out.data_ptr(), _stream_handle(stream, ids.device)),
+               "pospopcnt_onehot_counts")
+    return out
 
 
 def pospopcnt_count(width: int, x, kernel="auto", counts=None, stream=None):

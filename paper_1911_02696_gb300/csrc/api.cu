@@ -217,6 +217,7 @@ int launch_plain_k(const DeviceState&, const pospopcnt_config&, const void*, siz
 int launch_plain(const DeviceState& st, int width, const pospopcnt_config& cfg, const void* d_in, size_t n,
                  unsigned long long* d_counts, bool zero_first, cudaStream_t stream) {
   switch (width) {
+    case 1: return launch_plain_k<1>(st, cfg, d_in, n, d_counts, zero_first, stream);
     case 8: return launch_plain_k<8>(st, cfg, d_in, n, d_counts, zero_first, stream);
     case 16: return launch_plain_k<16>(st, cfg, d_in, n, d_counts, zero_first, stream);
     case 32: return launch_plain_k<32>(st, cfg, d_in, n, d_counts, zero_first, stream);
@@ -327,6 +328,19 @@ int pospopcnt_count_config(int width, const pospopcnt_config* cfg, const void* d
 int pospopcnt_count_accumulate(int width, const void* d_in, size_t n, uint64_t* d_counts,
                                cudaStream_t stream) {
   return count_impl(width, nullptr, false, d_in, n, d_counts, stream);
+}
+
+int pospopcnt_popcount(const void* d_in, size_t nbytes, uint64_t* d_count, cudaStream_t stream) {
+  if (!d_count || (nbytes > 0 && !d_in)) return POSPOPCNT_ERR_INVALID;
+  if (reinterpret_cast<uintptr_t>(d_count) % 8 != 0) return POSPOPCNT_ERR_MISALIGNED;
+  if (nbytes > (size_t(1) << 42)) return POSPOPCNT_ERR_TOO_LARGE;
+  int rc = POSPOPCNT_OK;
+  DeviceState* st = current_state(&rc);
+  if (!st) return rc;
+  // the launch shapes of the 16-bit count serve the single counter too
+  pospopcnt_config cfg = tuned_default(16, size_class(uint64_t(nbytes)));
+  if ((rc = normalize_config(*st, 16, &cfg)) != POSPOPCNT_OK) return rc;
+  return launch_plain(*st, 1, cfg, d_in, nbytes, reinterpret_cast<unsigned long long*>(d_count), true, stream);
 }
 
 int pospopcnt_count_host(int width, const void* h_in, size_t n, uint64_t* h_counts) {

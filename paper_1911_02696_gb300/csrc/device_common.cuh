@@ -31,6 +31,10 @@ struct ilog2<1> {
 template <int K>
 struct lane_mask;
 template <>
+struct lane_mask<1> {  // K = 1: the array popcount, every bit is position 0
+  static constexpr uint32_t value = 0xFFFFFFFFu;
+};
+template <>
 struct lane_mask<8> {
   static constexpr uint32_t value = 0x01010101u;
 };
@@ -96,16 +100,27 @@ __device__ __forceinline__ void finalize(uint32_t (&c)[K], const uint32_t (&top)
   }
 }
 
+// Bytes per word (K = 1, the array popcount, walks its head and tail byte
+// by byte).
+template <int K>
+struct word_bytes {
+  static constexpr int value = K == 1 ? 1 : K / 8;
+};
+
 // One word counted bit by bit (head and tail words, §4.1's residual).
 template <int K>
 __device__ __forceinline__ void count_word(uint32_t (&c)[K], uint32_t w) {
+  if constexpr (K == 1) {
+    c[0] += __popc(w);
+  } else {
 #pragma unroll
-  for (int p = 0; p < K; ++p) c[p] += (w >> p) & 1u;
+    for (int p = 0; p < K; ++p) c[p] += (w >> p) & 1u;
+  }
 }
 
 template <int K>
 __device__ __forceinline__ uint32_t load_word(const uint8_t* p) {
-  if constexpr (K == 8) return *p;
+  if constexpr (K == 8 || K == 1) return *p;
   if constexpr (K == 16) return *reinterpret_cast<const uint16_t*>(p);
   return *reinterpret_cast<const uint32_t*>(p);
 }
@@ -168,18 +183,18 @@ __device__ __forceinline__ uint32_t warp_reduce_positions(uint32_t (&v)[K]) {
 
 // Block reduction followed by one 64-bit atomic add per position per block,
 // or, when the block is the whole grid and the caller asked for it (store),
-// a plain store of every position (no prior memset needed).  Every thread of
-// the block must call it.
+// a plain store of every position (no prior memset needed).  Only positions
+// below `limit` are written.  Every thread of the block must call it.
 template <int K, int NWARPS>
 __device__ __forceinline__ void block_reduce_add(uint32_t (&c)[K], unsigned long long* counts,
-                                                 bool store = false) {
+                                                 bool store = false, int limit = K) {
   __shared__ uint32_t red[NWARPS][K];
   constexpr int SH = 5 - ilog2<K>::value;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t v = warp_reduce_positions<K>(c);
   if ((lane & ((1 << SH) - 1)) == 0) red[warp][lane >> SH] = v;
   __syncthreads();
-  if (threadIdx.x < K) {
+  if (int(threadIdx.x) < limit) {  // positions >= limit are not part of the output
     unsigned long long s = 0;
 #pragma unroll
     for (int w = 0; w < NWARPS; ++w) s += red[w][threadIdx.x];

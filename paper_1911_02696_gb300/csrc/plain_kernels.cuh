@@ -43,8 +43,9 @@ __device__ __forceinline__ void count_head_tail(uint32_t (&c)[K], const PlainArg
   static_assert(NTHREADS >= 64, "head/tail lanes need two warps");
   if (blockIdx.x != 0) return;
   const unsigned t = threadIdx.x;
-  if (t < a.head_words) count_word<K>(c, load_word<K>(a.head + t * (K / 8)));
-  if (t >= 32 && t - 32 < a.tail_words) count_word<K>(c, load_word<K>(a.tail + (t - 32) * (K / 8)));
+  constexpr int WB = word_bytes<K>::value;
+  if (t < a.head_words) count_word<K>(c, load_word<K>(a.head + t * WB));
+  if (t >= 32 && t - 32 < a.tail_words) count_word<K>(c, load_word<K>(a.tail + (t - 32) * WB));
 }
 
 // ---------------------------------------------------------------------------
@@ -420,14 +421,15 @@ static int launch_csa_u(const DeviceState& st, const PlainArgs& a, const pospopc
 
 template <int K>
 static PlainArgs make_args(const DeviceState& st, const void* d_in, size_t n, unsigned long long* d_counts) {
-  const Split sp = plan_split(K, reinterpret_cast<uint64_t>(d_in), n);
+  constexpr int WB = word_bytes<K>::value;
+  const Split sp = plan_split(8 * WB, reinterpret_cast<uint64_t>(d_in), n);
   const uint8_t* base = static_cast<const uint8_t*>(d_in);
   PlainArgs a;
   a.head = base;
   a.head_words = uint32_t(sp.head_words);
-  a.body = reinterpret_cast<const uint4*>(base + sp.head_words * (K / 8));
+  a.body = reinterpret_cast<const uint4*>(base + sp.head_words * WB);
   a.nvec = sp.body_vectors;
-  a.tail = base + sp.head_words * (K / 8) + sp.body_vectors * 16;
+  a.tail = base + sp.head_words * WB + sp.body_vectors * 16;
   a.tail_words = uint32_t(sp.tail_words);
   a.counts = d_counts;
   a.err = st.d_err;
@@ -463,18 +465,7 @@ static int launch_csa64(const DeviceState& st, PlainArgs a, int bps, bool zero_f
 template <int K>
 int launch_plain_k(const DeviceState& st, const pospopcnt_config& cfg, const void* d_in, size_t n,
                    unsigned long long* d_counts, bool zero_first, cudaStream_t stream) {
-  const Split sp = plan_split(K, reinterpret_cast<uint64_t>(d_in), n);
-  const uint8_t* base = static_cast<const uint8_t*>(d_in);
-  PlainArgs a;
-  a.head = base;
-  a.head_words = uint32_t(sp.head_words);
-  a.body = reinterpret_cast<const uint4*>(base + sp.head_words * (K / 8));
-  a.nvec = sp.body_vectors;
-  a.tail = base + sp.head_words * (K / 8) + sp.body_vectors * 16;
-  a.tail_words = uint32_t(sp.tail_words);
-  a.counts = d_counts;
-  a.err = st.d_err;
-  a.store = 0;
+  PlainArgs a = make_args<K>(st, d_in, n, d_counts);
   if (a.nvec == 0 && a.head_words == 0 && a.tail_words == 0) {
     if (!zero_first) return POSPOPCNT_OK;
     const cudaError_t e = cudaMemsetAsync(d_counts, 0, sizeof(unsigned long long) * K, stream);

@@ -62,6 +62,8 @@ def _load():
             lib.synth_one_hot.argtypes = [u64, i32, vp, vp, u64, vp, i32]
             lib.synth_sparse.restype = i32
             lib.synth_sparse.argtypes = [u64, i32, ctypes.c_uint32, vp, u64, i32]
+            lib.synth_categorical_ids.restype = i32
+            lib.synth_categorical_ids.argtypes = [u64, i32, vp, i32, vp, u64, i32]
             lib.synth_segmented_one_hot.restype = i32
             lib.synth_segmented_one_hot.argtypes = [u64, i32, vp, vp, vp, u64, vp, i32]
             _lib = lib
@@ -204,3 +206,15 @@ def serving_trace(seed: int, rate: float, duration: float, pool_bytes: int, min_
     span = pool_bytes - nbytes
     off = (rng.uniform(0, 1, size=n) * (span // wb + 1)).astype(np.int64) * wb
     return {"t_arrival": t.astype(np.float64), "width": w, "offset_bytes": off, "nwords": nwords.astype(np.uint64)}
+
+
+def categorical_ids(seed: int, n: int, cdf: np.ndarray, dtype=np.uint8, nthreads: int | None = None) -> np.ndarray:
+    """n category ids drawn from the categorical distribution `cdf` (scaled
+    to 2^32; len(cdf) categories), as unsigned integers of `dtype`."""
+    cdf = np.ascontiguousarray(cdf, dtype=np.uint64)
+    assert int(cdf[-1]) == 2 ** 32
+    out = np.empty(n, dtype=dtype)
+    if n:
+        assert _load().synth_categorical_ids(seed, cdf.size, _ptr(cdf), out.itemsize, _ptr(out), n,
+                                             _threads(nthreads)) == 0
+    return out

@@ -223,3 +223,31 @@ int synth_segmented_one_hot(uint64_t seed, int width, const uint64_t* cdf, const
   parallel_for(seg_range, &c, nseg, nthreads);
   return 0;
 }
+
+/* ---- categorical ids ------------------------------------------------------
+ * Id i takes the 32-bit uniform u = draw(i) >> 32 and is the smallest j with
+ * u < cdf[j] (cdf over m categories scaled to 2^32), stored little-endian in
+ * id_bytes bytes. */
+
+typedef struct {
+  uint64_t key;
+  int m, id_bytes;
+  const uint64_t* cdf;
+  unsigned char* out;
+} ids_ctx;
+
+static void ids_range(void* p, uint64_t lo, uint64_t hi) {
+  ids_ctx* c = (ids_ctx*)p;
+  for (uint64_t i = lo; i < hi; ++i) {
+    uint64_t u = draw(c->key, i) >> 32;
+    store_le(c->out + i * (uint64_t)c->id_bytes, c->id_bytes, (uint64_t)pick(c->cdf, c->m, u));
+  }
+}
+
+int synth_categorical_ids(uint64_t seed, int m, const uint64_t* cdf, int id_bytes, void* out, uint64_t n,
+                          int nthreads) {
+  if (m < 1 || (id_bytes != 1 && id_bytes != 2 && id_bytes != 4)) return -1;
+  ids_ctx c = {key_of(seed), m, id_bytes, cdf, (unsigned char*)out};
+  parallel_for(ids_range, &c, n, nthreads);
+  return 0;
+}

@@ -106,7 +106,10 @@ def test_argument_checks_need_no_device():
     assert lib.pospopcnt_count_accumulate(7, good, 5, good, None) == 1
     # too large
     assert lib.pospopcnt_u8(good, 1 << 43, good, None) == 6
-    # 64-bit words: 8-byte alignment; only the CSA family
+    # array popcount: null pointers, misaligned count
+    assert lib.pospopcnt_popcount(None, 5, good, None) == 1
+    assert lib.pospopcnt_popcount(good, 5, P((1 << 20) + 4), None) == 2
+    # 64-bit words: 8-byte alignment
     assert lib.pospopcnt_u64(P((1 << 20) + 4), 5, good, None) == 2
     # batched: nseg == 0 is a no-op; null pointers; bad width; misalignment
     assert lib.pospopcnt_batched(None, None, 0, 16, None, None) == 0

@@ -1,0 +1,73 @@
+"""Fused one-hot encode + count on the GPU against the oracle (which one-hot
+encodes each id and then counts positions, §1): every id width, k on both
+sides of the 8/16/32-bit lane boundaries, ids >= k present, every small
+length at every aligned start, ragged large sizes, skewed ids, 2 GiB."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+import paper_1911_02696_gb300 as ppc  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DT = {1: np.uint8, 2: np.uint16, 4: np.uint32}
+TORCH_DT = {1: torch.uint8, 2: torch.int16, 4: torch.int32}
+
+
+def _dev(ids, offset):
+    """Device copy of the ids, `offset` bytes past a 256-byte boundary, with
+    guard bytes around it."""
+    b = ids.view(np.uint8)
+    buf = torch.full((256 + offset + b.size + 256,), 0x07, dtype=torch.uint8, device="cuda")
+    if b.size:
+        buf[256 + offset: 256 + offset + b.size].copy_(torch.from_numpy(b))
+    x = buf[256 + offset: 256 + offset + b.size]
+    return x if ids.itemsize == 1 else x.view(TORCH_DT[ids.itemsize])
+
+
+def _run(ids, k, offset=0):
+    x = _dev(ids, offset)
+    full = torch.full((k + 4,), -9, dtype=torch.int64, device="cuda")
+    ppc.pospopcnt_onehot_counts(x, k, counts=full[:k])
+    torch.cuda.synchronize()
+    got = full.cpu().numpy()
+    assert np.all(got[k:] == -9)
+    return got[:k].view(np.uint64)
+
+
+@pytest.mark.parametrize("idb", [1, 2, 4])
+@pytest.mark.parametrize("k", [1, 3, 8, 9, 16, 17, 32])
+def test_small_lengths_every_offset(idb, k):
+    rng = np.random.default_rng(idb * 100 + k)
+    ids = rng.integers(0, 2 * k + 2, size=200).astype(DT[idb])
+    for offset in range(0, 16, idb):
+        for n in list(range(0, 40)) + [63, 64, 65, 127, 128, 129, 199, 200]:
+            assert np.array_equal(_run(ids[:n], k, offset), oracle.onehot_counts(ids[:n], k)), (offset, n)
+
+
+@pytest.mark.parametrize("idb", [1, 2, 4])
+def test_ragged_large_and_skewed(idb):
+    rng = np.random.default_rng(idb)
+    for k in (5, 16, 32):
+        for _ in range(3):
+            n = int(rng.integers(1, (24 << 20) // idb))
+            ids = synth.categorical_ids(int(rng.integers(1 << 30)), n, synth.zipf_cdf(min(2 * k, 64)), DT[idb])
+            off = int(rng.integers(0, 16 // idb)) * idb
+            assert np.array_equal(_run(ids, k, off), oracle.onehot_counts(ids, k))
+
+
+def test_rejects():
+    x = torch.zeros(16, dtype=torch.uint8, device="cuda")
+    for k in (0, 33):
+        with pytest.raises(ppc.PospopcntError):
+            ppc.pospopcnt_onehot_counts(x, k)
+
+
+@pytest.mark.slow
+def test_full_u8_ids_zipf16():
+    ids = synth.categorical_ids(0, 1 << 31, synth.zipf_cdf(16), np.uint8)
+    got = _run(ids, 16)
+    assert int(got.sum()) == 1 << 31
+    assert np.array_equal(got, oracle.onehot_counts(ids, 16))

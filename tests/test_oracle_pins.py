@@ -334,3 +334,46 @@ def test_pins_catch_mutant(name, golden_dir):
             except AssertionError:
                 failed.append(pin)
         assert failed, f"no pin caught mutant {name}"
+
+
+# --------------------------------------------------------------------------
+# array popcount (the single sum pospopcnt generalises)
+# --------------------------------------------------------------------------
+
+def test_popcount_pins():
+    assert oracle.popcount(np.zeros(0, dtype=np.uint8)) == 0
+    assert oracle.popcount(np.full(1000, 0xFF, dtype=np.uint8)) == 8000
+    assert oracle.popcount(np.arange(256, dtype=np.uint8)) == 1024  # each bit set in half of 256 bytes
+    for seed, n in ((1, 1), (2, 333), (3, 1 << 16)):
+        b = synth.uniform_bytes(seed, n)
+        ref = _popcount_total(b)  # independent library popcount
+        assert oracle.popcount(b) == ref
+        assert oracle.popcount(b) == int(oracle.pospopcnt(b, 8).sum())  # the sum of the positional counts
+
+
+# --------------------------------------------------------------------------
+# one-hot encode + count (the motivating pipeline of §1)
+# --------------------------------------------------------------------------
+
+def test_onehot_counts_table1(golden_dir):
+    """§1, Table 1: the stream as category ids (the one-hot positions) gives
+    France 3, Portugal 2, USA 4, China 1."""
+    mapping, stream, freq = load_table1(golden_dir)
+    pos = {name: code.bit_length() - 1 for name, code in mapping.items()}
+    ids = np.array([pos[name] for _, name in stream], dtype=np.uint8)
+    c = oracle.onehot_counts(ids, 8)
+    for name, p in pos.items():
+        assert int(c[p]) == freq.get(name, 0)
+
+
+@pytest.mark.parametrize("dt", [np.uint8, np.uint16, np.uint32])
+def test_onehot_counts_equal_bincount(dt):
+    rng = np.random.default_rng(3)
+    for k in (1, 5, 8, 13, 16, 32, 64):
+        ids = rng.integers(0, min(np.iinfo(dt).max, 3 * k) + 1, size=5000).astype(dt)
+        ref = np.bincount(ids[ids < k].astype(np.int64), minlength=k)[:k].astype(np.uint64)
+        assert np.array_equal(oracle.onehot_counts(ids, k), ref)
+        # and equals the positional count of the explicitly encoded words (k <= 32)
+        if k <= 32:
+            words = np.where(ids < k, np.uint64(1) << np.minimum(ids, 63).astype(np.uint64), 0).astype(np.uint32)
+            assert np.array_equal(oracle.onehot_counts(ids, k), oracle.pospopcnt(words, 32)[:k])

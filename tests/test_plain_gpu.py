@@ -306,3 +306,40 @@ def test_full_u64():
     _full(64, synth.uniform_bits(2, 1 << 28, 64), kernels=("auto", "csa", "tma"))
     ref = _full(64, synth.one_hot(2, 1 << 28, 64, cdf=synth.uniform_cdf(64)), kernels=("auto",))
     assert int(ref.sum()) == 1 << 28
+
+
+def test_popcount_small_lengths_every_offset():
+    """Array popcount (K = 1): n = 0..299 bytes at every start offset 0..15."""
+    b = synth.uniform_bytes(1, 300)
+    for offset in range(16):
+        _, x_all = _device_slice(b, offset)
+        out = torch.full((300, 2), SENTINEL, dtype=torch.int64, device="cuda")
+        for n in range(300):
+            ppc.pospopcnt_popcount(x_all[:n], count=out[n, :1])
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        for n in range(300):
+            assert int(got[n, 0]) == oracle.popcount(b[:n]), (offset, n)
+            assert got[n, 1] == SENTINEL
+
+
+def test_popcount_sizes_and_patterns():
+    rng = np.random.default_rng(11)
+    for _ in range(6):
+        n = int(rng.integers(1, 80 << 20))
+        b = synth.uniform_bytes(int(rng.integers(1 << 30)), n)
+        _, x = _device_slice(b, int(rng.integers(0, 16)))
+        got = int(ppc.pospopcnt_popcount(x).cpu()[0])
+        assert got == oracle.popcount(b)
+    ones = np.full((5 << 20) + 3, 0xFF, dtype=np.uint8)
+    _, x = _device_slice(ones, 5)
+    assert int(ppc.pospopcnt_popcount(x).cpu()[0]) == 8 * ones.size
+
+
+@pytest.mark.slow
+def test_popcount_full():
+    b = synth.uniform_bytes(5, 1 << 31)
+    _, x = _device_slice(b, 0)
+    got = int(ppc.pospopcnt_popcount(x).cpu()[0])
+    ref, _ = oracle.pospopcnt_mt(b, 8)
+    assert got == int(ref.sum())
