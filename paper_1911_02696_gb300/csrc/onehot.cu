@@ -29,13 +29,22 @@ struct OnehotArgs {
   uint32_t store;
 };
 
-// The j-th id of a 16-byte vector of IDB-byte ids (j known at compile time).
+// The j-th id of a 16-byte vector of IDB-byte ids (j known at compile time),
+// zero-extended with one byte permute.
 template <int IDB>
 __device__ __forceinline__ uint32_t id_at(const uint4& x, int j) {
   const uint32_t r[4] = {x.x, x.y, x.z, x.w};
   if constexpr (IDB == 4) return r[j];
-  if constexpr (IDB == 2) return (r[j / 2] >> (16 * (j % 2))) & 0xFFFFu;
-  return (r[j / 4] >> (8 * (j % 4))) & 0xFFu;
+  if constexpr (IDB == 2) return __byte_perm(r[j / 2], 0u, (j % 2) ? 0x4432u : 0x4410u);
+  return __byte_perm(r[j / 4], 0u, 0x4440u | unsigned(j % 4));
+}
+
+// base << amount with the PTX rule that amounts above 32 give 0, so an id
+// of 32 or more shifts the one-hot bit out of the register.
+__device__ __forceinline__ uint32_t shl_clamped(uint32_t base, uint32_t amount) {
+  uint32_t d;
+  asm("shl.b32 %0, %1, %2;" : "=r"(d) : "r"(base), "r"(amount));
+  return d;
 }
 
 template <int IDB>
@@ -52,6 +61,13 @@ __global__ void __launch_bounds__(NTHREADS) onehot_kernel(OnehotArgs a) {
   constexpr int REGS_PER_VEC = IDS_PER_VEC / IDS_PER_REG;
   constexpr int U = 16 / REGS_PER_VEC;  // vectors per trip: 16 registers, circuit F_4
   const uint32_t k = a.k;
+  // lane q of a register holds the one-hot bit of its id at bit q*LW + id;
+  // the mask keeps bits q*LW .. q*LW + k - 1 (ids >= k, which could spill
+  // into the next lane, are dropped)
+  const uint32_t km = k >= 32 ? 0xFFFFFFFFu : (1u << k) - 1u;
+  uint32_t lane_mask_q[IDS_PER_REG];
+#pragma unroll
+  for (int q = 0; q < IDS_PER_REG; ++q) lane_mask_q[q] = km << (q * LW);
   uint32_t B[4] = {0, 0, 0, 0};
   uint32_t top[LW];
 #pragma unroll
@@ -70,7 +86,7 @@ __global__ void __launch_bounds__(NTHREADS) onehot_kernel(OnehotArgs a) {
 #pragma unroll
         for (int q = 0; q < IDS_PER_REG; ++q) {
           const uint32_t id = id_at<IDB>(x, r * IDS_PER_REG + q);
-          reg |= id < k ? 1u << (id + uint32_t(q * LW)) : 0u;  // k <= LW: stays in its lane
+          reg |= shl_clamped(1u << (q * LW), id) & lane_mask_q[q];  // one shift, one masked or
         }
         d[i * REGS_PER_VEC + r] = live ? reg : 0u;
       }
