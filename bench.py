@@ -481,8 +481,10 @@ def run_batched(args, world, rank, local):
 
 def candidate_configs():
     cfgs = [dict(kernel="csa", threads=t, unroll=u) for t in (128, 256, 512) for u in (2, 4, 8)]
-    cfgs += [dict(kernel="tma", stages=st, chunk_bytes=c) for st in (2, 3, 4, 6, 8)
-             for c in (16384, 32768, 65536) if st * c <= 196608]
+    cfgs += [dict(kernel="tma", stages=st, chunk_bytes=c, flags=fl) for st in (2, 3, 4, 6, 8)
+             for c in (16384, 32768, 49152, 65536, 98304) for fl in (0, 1) if st * c <= 196608]
+    cfgs += [dict(kernel="tma", stages=3, chunk_bytes=32768, blocks_per_sm=2, flags=fl) for fl in (0, 1)]
+    cfgs += [dict(kernel="tma", stages=2, chunk_bytes=49152, blocks_per_sm=2, flags=fl) for fl in (0, 1)]
     cfgs += [dict(kernel="ballot", unroll=u) for u in (1, 2, 4)]
     return cfgs
 

@@ -73,7 +73,12 @@ typedef struct {
   int blocks_per_sm;
   int stages;
   int chunk_bytes;
+  int flags;  /* POSPOPCNT_FLAG_* bits (0: none) */
 } pospopcnt_config;
+
+/* TMA family: the bulk copies carry an L2 evict-first policy (every input
+ * byte is read exactly once, so its lines need not stay in L2). */
+#define POSPOPCNT_FLAG_EVICT_FIRST 1
 
 /* Creates the per-device state of `device` (error word, queue slots, SM
  * count).  Idempotent.  Makes `device` current only for the duration of

@@ -48,9 +48,10 @@ class PospopcntError(RuntimeError):
 
 
 class Config(ctypes.Structure):
-    """pospopcnt_config: kernel, threads, unroll, blocks_per_sm, stages, chunk_bytes."""
+    """pospopcnt_config: kernel, threads, unroll, blocks_per_sm, stages, chunk_bytes, flags."""
     _fields_ = [("kernel", ctypes.c_int), ("threads", ctypes.c_int), ("unroll", ctypes.c_int),
-                ("blocks_per_sm", ctypes.c_int), ("stages", ctypes.c_int), ("chunk_bytes", ctypes.c_int)]
+                ("blocks_per_sm", ctypes.c_int), ("stages", ctypes.c_int), ("chunk_bytes", ctypes.c_int),
+                ("flags", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -46,6 +46,7 @@ pospopcnt_config default_config() {
   c.blocks_per_sm = 0;
   c.stages = 4;
   c.chunk_bytes = 32768;
+  c.flags = 0;
   return c;
 }
 
@@ -177,6 +178,7 @@ int normalize_config(const DeviceState& st, int width, pospopcnt_config* c) {
   if (c->kernel == POSPOPCNT_KERNEL_AUTO) c->kernel = d.kernel;
   if (c->threads == 0) c->threads = 256;
   if (c->blocks_per_sm < 0 || c->blocks_per_sm > 32) return POSPOPCNT_ERR_INVALID;
+  if (c->flags & ~POSPOPCNT_FLAG_EVICT_FIRST) return POSPOPCNT_ERR_INVALID;
   if (width == 64 && c->kernel != POSPOPCNT_KERNEL_TMA) {  // 64-bit words: CSA 128/256 threads, unroll 4/8
     if (c->unroll == 0) c->unroll = 8;
     if (c->kernel != POSPOPCNT_KERNEL_CSA || (c->threads != 128 && c->threads != 256) ||
@@ -520,11 +522,12 @@ int pospopcnt_autotune(int width, const void* d_in, size_t n, uint64_t* d_scratc
       if (normalize_config(*st, width, &c) == POSPOPCNT_OK) cands.push_back(c);
     }
   for (int s : {2, 3, 4, 6, 8})
-    for (int ch : {16384, 32768, 65536}) {
-      pospopcnt_config c = default_config();
-      c.kernel = POSPOPCNT_KERNEL_TMA, c.stages = s, c.chunk_bytes = ch;
-      if (normalize_config(*st, width, &c) == POSPOPCNT_OK) cands.push_back(c);
-    }
+    for (int ch : {16384, 32768, 49152, 65536, 98304})
+      for (int fl : {0, POSPOPCNT_FLAG_EVICT_FIRST}) {
+        pospopcnt_config c = default_config();
+        c.kernel = POSPOPCNT_KERNEL_TMA, c.stages = s, c.chunk_bytes = ch, c.flags = fl;
+        if (normalize_config(*st, width, &c) == POSPOPCNT_OK) cands.push_back(c);
+      }
   cudaStream_t s = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e;

@@ -104,6 +104,7 @@ struct TmaArgs {
   uint64_t body_bytes;  // multiple of 16
   uint32_t chunk_bytes;  // multiple of TMA_CHUNK_QUANTUM
   uint32_t stages;
+  uint32_t evict_first;  // L2 evict-first hint on the bulk copies
 };
 
 // Register classes of the TMA consumers: for K <= 32 every 32-bit register
@@ -155,6 +156,7 @@ __global__ void __launch_bounds__(TMA_THREADS) tma_kernel(TmaArgs a) {
   if (warp == TMA_CWARPS) {
     // producer: one lane issues every copy
     if (lane == 0) {
+      const uint64_t policy = a.evict_first ? l2_policy_evict_first() : 0;
       uint32_t i = 0;
       for (; i < my_chunks; ++i) {
         const uint32_t s = i % S_, use = i / S_;
@@ -169,7 +171,10 @@ __global__ void __launch_bounds__(TMA_THREADS) tma_kernel(TmaArgs a) {
         const uint64_t rem = a.body_bytes - off;
         const uint32_t bytes = rem < a.chunk_bytes ? uint32_t(rem) : a.chunk_bytes;
         mbar_arrive_expect_tx(&full[s], bytes);
-        bulk_g2s(ring + size_t(s) * a.chunk_bytes, a.body_bytes_ptr + off, bytes, &full[s]);
+        if (a.evict_first)
+          bulk_g2s_hint(ring + size_t(s) * a.chunk_bytes, a.body_bytes_ptr + off, bytes, &full[s], policy);
+        else
+          bulk_g2s(ring + size_t(s) * a.chunk_bytes, a.body_bytes_ptr + off, bytes, &full[s]);
       }
       s_issued = i;
     }
@@ -385,7 +390,7 @@ static int launch_ballot(const DeviceState& st, PlainArgs a, int bps, bool zero_
 
 template <int K>
 static int launch_tma(const DeviceState& st, const PlainArgs& p, int bps, int stages, int chunk, bool zero_first,
-                      cudaStream_t stream) {
+                      cudaStream_t stream, int flags = 0) {
   auto kern = tma_kernel<K>;
   const size_t smem = size_t(stages) * size_t(chunk);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
@@ -396,6 +401,7 @@ static int launch_tma(const DeviceState& st, const PlainArgs& p, int bps, int st
   a.body_bytes = p.nvec * 16;
   a.chunk_bytes = uint32_t(chunk);
   a.stages = uint32_t(stages);
+  a.evict_first = (flags & POSPOPCNT_FLAG_EVICT_FIRST) ? 1u : 0u;
   const int occ = occupancy(kern, TMA_THREADS, smem);
   const uint64_t cap = uint64_t(st.sms) * uint64_t(std::min(bps > 0 ? bps : occ, occ));
   const uint64_t nchunks = (a.body_bytes + chunk - 1) / chunk;
@@ -474,7 +480,7 @@ int launch_plain_k(const DeviceState& st, const pospopcnt_config& cfg, const voi
   if constexpr (K == 64) {  // 64-bit words: the CSA and TMA families
     if (cfg.kernel == POSPOPCNT_KERNEL_TMA) {
       if (a.nvec == 0) return launch_csa64<4, 256>(st, a, 1, zero_first, stream);  // head/tail only
-      return launch_tma<K>(st, a, cfg.blocks_per_sm, cfg.stages, cfg.chunk_bytes, zero_first, stream);
+      return launch_tma<K>(st, a, cfg.blocks_per_sm, cfg.stages, cfg.chunk_bytes, zero_first, stream, cfg.flags);
     }
     switch (cfg.threads) {
       case 128: return cfg.unroll == 8 ? launch_csa64<8, 128>(st, a, cfg.blocks_per_sm, zero_first, stream)
@@ -494,7 +500,7 @@ int launch_plain_k(const DeviceState& st, const pospopcnt_config& cfg, const voi
       return POSPOPCNT_ERR_INVALID;
     case POSPOPCNT_KERNEL_TMA:
       if (a.nvec == 0) return launch_csa<K, 4, 256>(st, a, 1, zero_first, stream);  // head/tail only
-      return launch_tma<K>(st, a, cfg.blocks_per_sm, cfg.stages, cfg.chunk_bytes, zero_first, stream);
+      return launch_tma<K>(st, a, cfg.blocks_per_sm, cfg.stages, cfg.chunk_bytes, zero_first, stream, cfg.flags);
     case POSPOPCNT_KERNEL_BALLOT:
       switch (cfg.unroll) {
         case 1: return launch_ballot<K, 1, 256>(st, a, cfg.blocks_per_sm, zero_first, stream);

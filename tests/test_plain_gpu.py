@@ -110,8 +110,8 @@ def test_every_config(width):
     """Every configuration the autotuner may pick gives the same counts."""
     words = synth.uniform_bits(77, (9 << 20) // (width // 8) + 3, width)
     cfgs = [dict(kernel="csa", threads=t, unroll=u) for t in (128, 256, 512) for u in (2, 4, 8)]
-    cfgs += [dict(kernel="tma", stages=s, chunk_bytes=c) for s in (2, 3, 4, 6, 8)
-             for c in (16384, 32768, 65536) if s * c <= 196608]
+    cfgs += [dict(kernel="tma", stages=s, chunk_bytes=c, flags=f) for s in (2, 3, 4, 6, 8)
+             for c in (16384, 32768, 49152, 65536, 98304) for f in (0, 1) if s * c <= 196608]
     cfgs += [dict(kernel="ballot", unroll=u) for u in (1, 2, 4)]
     cfgs += [dict(kernel="csa", blocks_per_sm=1), dict(kernel="tma", blocks_per_sm=1, stages=2)]
     for cfg in cfgs:
