@@ -54,9 +54,10 @@ pospopcnt_config default_config() {
 // autotuner run on a GB300 (152 SMs, 2070 MHz): below 256 KiB one wide CTA
 // (512 threads x 8 vectors covers 64 KiB in one trip, and a one-CTA grid
 // stores its counts without a memset); up to 64 MiB the register-load CSA
-// kernel; from 64 MiB (u16, u32) the bulk-copy ring, 3 stages x 64 KiB from
-// 256 MiB; u8 keeps the CSA kernel with 512-thread CTAs (its flush is the
-// cheapest, and the register path measured fastest at 1-4 GiB).
+// kernel; from 64 MiB (u16, u32) and 256 MiB (u8) the bulk-copy ring with
+// ~192 KiB per SM in flight (u16 4 x 48 KiB, u32 3 x 64 KiB, u8 4 x 32 KiB).
+// Every ring shape with that much in flight measured within 1.5 % of the
+// others at 2 GiB: the kernel is at the DRAM limit there.
 pospopcnt_config tuned_default(int width, int cls) {
   pospopcnt_config c = default_config();
   if (width == 64) {  // two circuits per thread; the bulk-copy ring from 64 MiB
@@ -76,6 +77,10 @@ pospopcnt_config tuned_default(int width, int cls) {
     return c;
   }
   if (width == 8) {
+    if (cls >= 14) {  // 256 MiB and up: the ring, 4 x 32 KiB
+      c.kernel = POSPOPCNT_KERNEL_TMA, c.stages = 4, c.chunk_bytes = 32768;
+      return c;
+    }
     c.threads = cls >= 13 ? 512 : 256;
     c.unroll = 4;
     return c;
@@ -85,8 +90,13 @@ pospopcnt_config tuned_default(int width, int cls) {
     return c;
   }
   c.kernel = POSPOPCNT_KERNEL_TMA;
-  c.stages = cls == 13 ? 2 : 3;
-  c.chunk_bytes = cls == 13 ? 32768 : 65536;
+  if (cls == 13) {
+    c.stages = 2, c.chunk_bytes = 32768;
+  } else if (width == 16) {
+    c.stages = 4, c.chunk_bytes = 49152;  // 192 KiB in flight per SM
+  } else {
+    c.stages = 3, c.chunk_bytes = 65536;
+  }
   return c;
 }
 
