@@ -170,11 +170,11 @@ int pospopcnt_batched(const void* d_in, const int64_t* d_offsets, size_t nseg, i
  * of the library, not of the method.  Same arguments, layout and result as
  * pospopcnt_batched; it calls no cudaMalloc, cudaFree or other allocating
  * routine, and needs no pospopcnt_init.  Its scratch (the work-queue state
- * of one launch, 16 bytes) is a 256-byte static device array that every GPU
- * which loads the library holds until the process exits; a call whose
- * scratch need exceeded 256 bytes would be rejected with
- * POSPOPCNT_ERR_TOO_LARGE (the need does not grow with the input, so every
- * input size fits).  The first call on a device looks up the array's device
+ * of one launch, 16 bytes, and a word where a bounded device wait records a
+ * timeout) lives in a 256-byte static device array that every GPU which
+ * loads the library holds until the process exits; a call whose scratch
+ * need exceeded 256 bytes would be rejected with POSPOPCNT_ERR_TOO_LARGE
+ * (the need does not grow with the input, so every input size fits).  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress, with that device current): make that first
  * call before any stream capture.  Every call on a device shares the one
  * array and clears it on its stream before launching, so calls that overlap

@@ -40,24 +40,141 @@ struct BatchedArgs {
   QueueSlot* q;
   uint64_t tile_words;        // multiple of 8 warps x 16 bytes
   const uint64_t* seg_addr;  // nullptr: offsets form
+  unsigned* err;             // device error word (bounded waits)
 };
+
+// Per-warp bulk-copy ring: lane 0 streams the 16-byte-aligned body of a long
+// piece into RING_STAGES shared-memory stages of one trip (32 lanes x 8
+// vectors) each, one mbarrier per stage; the warp counts from shared memory
+// while the next trips are in flight.
+constexpr int RING_STAGES = 3;
+constexpr int TRIP_VECS = 32 * BT_VPL;
+constexpr int TRIP_BYTES = TRIP_VECS * 16;
+constexpr int RING_MIN_VECS = 2 * TRIP_VECS;  // shorter bodies are loaded directly
+constexpr size_t BT_RING_SMEM = size_t(BT_WARPS) * RING_STAGES * TRIP_BYTES;
+
+struct WarpRing {
+  uint8_t* buf;    // RING_STAGES x TRIP_BYTES
+  uint64_t* full;  // RING_STAGES barriers
+  uint32_t seq;    // trips issued (and consumed) by this warp so far
+};
+
+// warp_piece_counts with the body streamed through the warp's ring when it
+// is long enough.  Returns false (after recording the error) if a bounded
+// wait gave up; the warp then stops counting.
+template <int K>
+__device__ __forceinline__ bool warp_piece_counts_ring(const uint8_t* base, uint64_t pa, uint64_t pb,
+                                                       WarpRing& r, unsigned* err, uint32_t& out) {
+  constexpr int WB = K / 8;
+  constexpr int R = 4 * BT_VPL;
+  constexpr int L = ilog2<R>::value;
+  const int lane = threadIdx.x & 31;
+  const uint64_t A = reinterpret_cast<uint64_t>(base) + pa * WB;
+  const uint64_t E = reinterpret_cast<uint64_t>(base) + pb * WB;
+  uint64_t bodyA = (A + 15) & ~uint64_t(15);
+  if (bodyA > E) bodyA = E;
+  uint64_t bodyE = E & ~uint64_t(15);
+  if (bodyE < bodyA) bodyE = bodyA;
+  const uint64_t nvec = (bodyE - bodyA) / 16;
+  if (nvec < RING_MIN_VECS) {
+    out = warp_piece_counts<K, BT_VPL>(base, pa, pb);
+    return true;
+  }
+  const uint32_t head_words = uint32_t((bodyA - A) / WB);
+  const uint32_t tail_words = uint32_t((E - bodyE) / WB);
+  uint32_t edge = 0;
+  if (uint32_t(lane) < head_words)
+    edge = load_word<K>(reinterpret_cast<const uint8_t*>(A) + lane * WB);
+  else if (lane >= 16 && uint32_t(lane - 16) < tail_words)
+    edge = load_word<K>(reinterpret_cast<const uint8_t*>(bodyE) + (lane - 16) * WB);
+
+  const uint4* src = reinterpret_cast<const uint4*>(bodyA);
+  const uint32_t ntrips = uint32_t((nvec + TRIP_VECS - 1) / TRIP_VECS);
+  auto issue = [&](uint32_t t) {  // lane 0 only
+    const uint32_t s = (r.seq + t) % RING_STAGES;
+    const uint64_t left = nvec - uint64_t(t) * TRIP_VECS;
+    const uint32_t bytes = uint32_t(left < TRIP_VECS ? left : TRIP_VECS) * 16u;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier reads of the stage first
+    mbar_arrive_expect_tx(&r.full[s], bytes);
+    bulk_g2s(r.buf + size_t(s) * TRIP_BYTES, src + uint64_t(t) * TRIP_VECS, bytes, &r.full[s]);
+  };
+  if (lane == 0)
+    for (uint32_t t = 0; t < ntrips && t < uint32_t(RING_STAGES); ++t) issue(t);
+
+  uint32_t B[L];
+#pragma unroll
+  for (int l = 0; l < L; ++l) B[l] = 0;
+  uint32_t top[K];
+#pragma unroll
+  for (int p = 0; p < K; ++p) top[p] = 0;
+  for (uint32_t t = 0; t < ntrips; ++t) {
+    const uint32_t seq = r.seq + t;
+    const uint32_t s = seq % RING_STAGES;
+    const bool ok = __all_sync(FULL_MASK, mbar_wait_bounded(&r.full[s], (seq / RING_STAGES) & 1u, WAIT_LIMIT_NS));
+    if (!ok) {
+      if (lane == 0) {
+        atomicOr(err, ERR_BIT_TIMEOUT_FULL);
+        // wait (bounded) for the copies still in flight into this warp's ring
+        for (uint32_t u = t; u < ntrips && u < t + RING_STAGES; ++u)
+          if (!mbar_wait_bounded(&r.full[(r.seq + u) % RING_STAGES], ((r.seq + u) / RING_STAGES) & 1u,
+                                 WAIT_LIMIT_NS)) {
+            atomicOr(err, ERR_BIT_TIMEOUT_DRAIN);
+            break;
+          }
+      }
+      __syncwarp();
+      return false;
+    }
+    const uint64_t left = nvec - uint64_t(t) * TRIP_VECS;
+    const uint32_t nv = uint32_t(left < TRIP_VECS ? left : TRIP_VECS);
+    const uint4* sv = reinterpret_cast<const uint4*>(r.buf + size_t(s) * TRIP_BYTES);
+    uint32_t d[R];
+#pragma unroll
+    for (int j = 0; j < BT_VPL; ++j) {
+      const uint32_t idx = uint32_t(j) * 32 + uint32_t(lane);
+      const uint4 x = idx < nv ? sv[idx] : make_uint4(0, 0, 0, 0);
+      d[4 * j + 0] = x.x, d[4 * j + 1] = x.y, d[4 * j + 2] = x.z, d[4 * j + 3] = x.w;
+    }
+    flush<K>(top, Circuit<L>::run(d, B));
+    __syncwarp();  // every lane has read the stage
+    if (lane == 0 && t + RING_STAGES < ntrips) issue(t + RING_STAGES);
+  }
+  r.seq += ntrips;
+  uint32_t c[K];
+  finalize<K, L>(c, top, B);
+  count_word<K>(c, edge);
+  out = warp_reduce_positions<K>(c);
+  return true;
+}
 
 
 // Counts words [pa, pb) of `base` with the whole warp and adds the result to
-// row[0..K-1].
+// row[0..K-1]; false if a bounded wait gave up.
 template <int K>
-__device__ __forceinline__ void warp_count_piece(const uint8_t* base, uint64_t pa, uint64_t pb,
-                                                 unsigned long long* row) {
+__device__ __forceinline__ bool warp_count_piece(const uint8_t* base, uint64_t pa, uint64_t pb,
+                                                 unsigned long long* row, WarpRing& ring, unsigned* err) {
   constexpr int SH = 5 - ilog2<K>::value;
   const int lane = threadIdx.x & 31;
-  const uint32_t v = warp_piece_counts<K, BT_VPL>(base, pa, pb);
+  uint32_t v = 0;
+  if (!warp_piece_counts_ring<K>(base, pa, pb, ring, err, v)) return false;
   if ((lane & ((1 << SH) - 1)) == 0 && v) atomicAdd(row + (lane >> SH), (unsigned long long)v);
+  return true;
 }
 
 template <int K>
 __global__ void __launch_bounds__(BT_THREADS, bt_batched_min_blocks<K>::value) batched_kernel(BatchedArgs a) {
   constexpr int WB = K / 8;
+  extern __shared__ __align__(128) uint8_t bt_ring[];
+  __shared__ __align__(8) uint64_t bt_full[BT_WARPS][RING_STAGES];
   const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  WarpRing ring{bt_ring + size_t(warp) * RING_STAGES * TRIP_BYTES, bt_full[warp], 0};
+  if (lane == 0) {
+    for (int s = 0; s < RING_STAGES; ++s) mbar_init(&ring.full[s], 1);
+    mbar_fence_init();
+  }
+  __syncwarp();
+  bool failed = false;
   const int64_t o0 = a.offsets[0];
   const int64_t oN = a.offsets[a.nseg];
   // offsets form: units start at the 16-byte boundary at or before word o0,
@@ -72,7 +189,7 @@ __global__ void __launch_bounds__(BT_THREADS, bt_batched_min_blocks<K>::value) b
   // Guided self-scheduling per warp: take about 1/(2 nwarps) of the units
   // still unclaimed (at least one), so early grabs are large, late ones
   // small, and no warp waits for another.
-  for (;;) {
+  while (!failed) {
     uint64_t u0 = 0, u1 = 0;
     if (lane == 0) {
       const uint64_t seen = *reinterpret_cast<volatile unsigned long long*>(&a.q->next);
@@ -98,7 +215,10 @@ __global__ void __launch_bounds__(BT_THREADS, bt_batched_min_blocks<K>::value) b
       if (pa < pb) {
         const uint8_t* pbase =
             a.seg_addr ? reinterpret_cast<const uint8_t*>(a.seg_addr[s] - uint64_t(seg_lo) * WB) : a.base;
-        warp_count_piece<K>(pbase, uint64_t(pa), uint64_t(pb), a.counts + s * K);
+        if (!warp_count_piece<K>(pbase, uint64_t(pa), uint64_t(pb), a.counts + s * K, ring, a.err)) {
+          failed = true;
+          break;
+        }
       }
       if (seg_hi >= w1 || s + 1 >= a.nseg) break;
       ++s;
@@ -111,11 +231,13 @@ __global__ void __launch_bounds__(BT_THREADS, bt_batched_min_blocks<K>::value) b
 template <int K>
 static int launch_batched_k(const DeviceState& st, const BatchedArgs& a, cudaStream_t stream) {
   auto kern = batched_kernel<K>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(BT_RING_SMEM)) != cudaSuccess)
+    return cuda_fail(cudaGetLastError());
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, BT_THREADS, 0) != cudaSuccess || occ < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, BT_THREADS, BT_RING_SMEM) != cudaSuccess || occ < 1)
     occ = 1;
   const unsigned grid = unsigned(st.sms) * unsigned(occ);
-  kern<<<grid, BT_THREADS, 0, stream>>>(a);
+  kern<<<grid, BT_THREADS, BT_RING_SMEM, stream>>>(a);
   note_launch();
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? POSPOPCNT_OK : cuda_fail(e);
@@ -132,6 +254,7 @@ int launch_batched(const DeviceState& st, const void* d_in, const int64_t* d_off
   a.counts = d_counts;
   a.q = static_cast<QueueSlot*>(queue_slot);
   a.tile_words = uint64_t(tile_words);
+  a.err = st.d_err;
   switch (width) {
     case 8: return launch_batched_k<8>(st, a, stream);
     case 16: return launch_batched_k<16>(st, a, stream);
@@ -225,6 +348,7 @@ extern "C" int pospopcnt_batched_noalloc(const void* d_in, const int64_t* d_offs
   a.counts = reinterpret_cast<unsigned long long*>(d_counts);
   a.q = static_cast<QueueSlot*>(scratch);
   a.tile_words = uint64_t((16 * 1024) / (width / 8));
+  a.err = reinterpret_cast<unsigned*>(static_cast<char*>(scratch) + 128);  // rest of the static array
   switch (width) {
     case 8: return launch_batched_k<8>(st, a, stream);
     case 16: return launch_batched_k<16>(st, a, stream);
