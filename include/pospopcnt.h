@@ -164,6 +164,16 @@ int pospopcnt_host_is_mapped(const void* h_in, size_t nbytes);
 int pospopcnt_batched(const void* d_in, const int64_t* d_offsets, size_t nseg, int width,
                       uint64_t* d_counts, cudaStream_t stream);
 
+/* pospopcnt_batched with the offsets checked on the device first: d_in
+ * holds n_words words; unless offsets[0] >= 0, the offsets are
+ * nondecreasing and offsets[nseg] <= n_words, nothing is counted (the rows
+ * stay zero) and the device error word records it, so that
+ * pospopcnt_check_device_error reports POSPOPCNT_ERR_INVALID.  Bad offsets
+ * thus become an error status instead of reads outside d_in.  Costs one
+ * small extra kernel over the offsets. */
+int pospopcnt_batched_checked(const void* d_in, size_t n_words, const int64_t* d_offsets, size_t nseg,
+                              int width, uint64_t* d_counts, cudaStream_t stream);
+
 /* pospopcnt_batched for callers that cannot allocate device memory (their
  * memory belongs to another runtime's pool allocator, or they must not
  * allocate once running).  The paper has no counterpart: this is a property
@@ -270,8 +280,9 @@ int pospopcnt_admission_simulate(uint64_t budget, size_t n, const double* t_arri
                                  const double* service_s, double* t_admit_out, int* status_out);
 
 /* Synchronises `stream`, reads and clears the device error word (set by a
- * bounded wait that gave up).  Returns POSPOPCNT_OK or
- * POSPOPCNT_ERR_TIMEOUT. */
+ * bounded wait that gave up, or by the offsets check of
+ * pospopcnt_batched_checked).  Returns POSPOPCNT_OK, POSPOPCNT_ERR_INVALID
+ * (bad offsets only) or POSPOPCNT_ERR_TIMEOUT. */
 int pospopcnt_check_device_error(cudaStream_t stream);
 
 /* Host-only planning of the head/body/tail split (§4.1 residual handling):

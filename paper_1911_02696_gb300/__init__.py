@@ -24,7 +24,7 @@ __all__ = [
     "PospopcntError", "load", "pospopcnt_init", "pospopcnt_u8", "pospopcnt_u16", "pospopcnt_u32", "pospopcnt_u64", "pospopcnt_popcount", "pospopcnt_onehot_counts",
     "pospopcnt_count", "pospopcnt_count_config", "pospopcnt_count_accumulate", "pospopcnt_count_host",
     "pospopcnt_host_is_mapped",
-    "pospopcnt_batched", "pospopcnt_batched_noalloc", "pospopcnt_plain_segments", "pospopcnt_check_device_error", "pospopcnt_plan_split",
+    "pospopcnt_batched", "pospopcnt_batched_checked", "pospopcnt_batched_noalloc", "pospopcnt_plain_segments", "pospopcnt_check_device_error", "pospopcnt_plan_split",
     "pospopcnt_get_config", "pospopcnt_set_config", "pospopcnt_autotune", "pospopcnt_strerror",
     "pospopcnt_last_cuda_error", "pospopcnt_launch_count", "pospopcnt_selftest_timeout", "KERNELS",
     "Config", "pospopcnt_server_create", "pospopcnt_server_destroy", "pospopcnt_server_submit",
@@ -122,6 +122,7 @@ def _declare(lib):
         "pospopcnt_batched": (i32, [vp, vp, sz, i32, vp, vp]),
         "pospopcnt_plain_segments": (i32, [vp, vp, sz, i32, vp, vp]),
         "pospopcnt_batched_noalloc": (i32, [vp, vp, sz, i32, vp, vp]),
+        "pospopcnt_batched_checked": (i32, [vp, sz, vp, sz, i32, vp, vp]),
         "pospopcnt_check_device_error": (i32, [vp]),
         "pospopcnt_plan_split": (i32, [i32, u64, sz, P(sz), P(sz), P(sz)]),
         "pospopcnt_get_config": (i32, [i32, sz, P(Config)]),
@@ -332,6 +333,22 @@ def pospopcnt_batched(x, offsets, width: int, counts=None, stream=None):
     with torch.cuda.device(x.device):
         _check(_lib().pospopcnt_batched(ptr, offsets.data_ptr(), nseg, width, out.data_ptr(),
                                         _stream_handle(stream, x.device)), "pospopcnt_batched")
+    return out
+
+
+def pospopcnt_batched_checked(x, offsets, width: int, counts=None, stream=None):
+    """pospopcnt_batched with the offsets validated on the device against
+    the words of x; bad offsets count nothing and are reported by
+    pospopcnt_check_device_error (status 1)."""
+    torch = _torch()
+    ptr, n_words = _words(x, width)
+    if offsets.dtype != torch.int64 or not offsets.is_cuda or not offsets.is_contiguous():
+        raise ValueError("offsets must be a contiguous CUDA int64 tensor")
+    nseg = max(offsets.numel() - 1, 0)
+    out = _counts_out(counts, width, nseg, x.device)
+    with torch.cuda.device(x.device):
+        _check(_lib().pospopcnt_batched_checked(ptr, n_words, offsets.data_ptr(), nseg, width, out.data_ptr(),
+                                                _stream_handle(stream, x.device)), "pospopcnt_batched_checked")
     return out
 
 

@@ -9,6 +9,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "device_common.cuh"
 #include "internal.h"
 #include "pospopcnt.h"
 
@@ -419,8 +420,29 @@ int pospopcnt_host_is_mapped(const void* h_in, size_t nbytes) {
   return mapped_device_view(h_in, nbytes) ? 1 : 0;
 }
 
+namespace ppc {
+namespace {
+int batched_impl(const void* d_in, const int64_t* d_offsets, size_t nseg, int width, uint64_t* d_counts,
+                 cudaStream_t stream, bool checked, uint64_t n_words);
+}  // namespace
+}  // namespace ppc
+
 int pospopcnt_batched(const void* d_in, const int64_t* d_offsets, size_t nseg, int width, uint64_t* d_counts,
                       cudaStream_t stream) {
+  return ppc::batched_impl(d_in, d_offsets, nseg, width, d_counts, stream, false, 0);
+}
+
+int pospopcnt_batched_checked(const void* d_in, size_t n_words, const int64_t* d_offsets, size_t nseg, int width,
+                              uint64_t* d_counts, cudaStream_t stream) {
+  return ppc::batched_impl(d_in, d_offsets, nseg, width, d_counts, stream, true, n_words);
+}
+
+}  // extern "C"
+
+namespace ppc {
+namespace {
+int batched_impl(const void* d_in, const int64_t* d_offsets, size_t nseg, int width, uint64_t* d_counts,
+                 cudaStream_t stream, bool checked, uint64_t n_words) {
   if (width != 8 && width != 16 && width != 32) return POSPOPCNT_ERR_INVALID;
   if (nseg == 0) return POSPOPCNT_OK;
   if (!d_in || !d_offsets || !d_counts) return POSPOPCNT_ERR_INVALID;
@@ -447,10 +469,15 @@ int pospopcnt_batched(const void* d_in, const int64_t* d_offsets, size_t nseg, i
   cudaError_t e = cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * size_t(width) * nseg, stream);
   if (e != cudaSuccess) return cuda_fail(e);
   void* q = static_cast<char*>(st->d_queue) + size_t(slot) * QUEUE_SLOT_BYTES;
+  if (checked && (rc = launch_offsets_check(*st, d_offsets, nseg, n_words, q, stream)) != POSPOPCNT_OK) return rc;
   const int tile_words = (16 * 1024) / (width / 8);  // 16 KiB scheduling unit
   return launch_batched(*st, d_in, d_offsets, nseg, width, reinterpret_cast<unsigned long long*>(d_counts), q,
                         tile_words, stream);
 }
+}  // namespace
+}  // namespace ppc
+
+extern "C" {
 
 int pospopcnt_plain_segments(const void* d_in, const int64_t* h_offsets, size_t nseg, int width,
                              uint64_t* d_counts, cudaStream_t stream) {
@@ -479,7 +506,8 @@ int pospopcnt_check_device_error(cudaStream_t stream) {
   if ((e = cudaMemcpy(&h, st->d_err, sizeof h, cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(e);
   if (h) {
     if ((e = cudaMemset(st->d_err, 0, sizeof h)) != cudaSuccess) return cuda_fail(e);
-    return POSPOPCNT_ERR_TIMEOUT;
+    return (h & ERR_BIT_BAD_OFFSETS) && !(h & ~unsigned(ERR_BIT_BAD_OFFSETS)) ? POSPOPCNT_ERR_INVALID
+                                                                                : POSPOPCNT_ERR_TIMEOUT;
   }
   return POSPOPCNT_OK;
 }

@@ -168,6 +168,10 @@ __global__ void __launch_bounds__(BT_THREADS, bt_batched_min_blocks<K>::value) b
   __shared__ __align__(8) uint64_t bt_full[BT_WARPS][RING_STAGES];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
+  if (*reinterpret_cast<volatile unsigned*>(&a.q->bad)) {  // the offsets check failed: touch no input
+    retire_cta(a.q);
+    return;
+  }
   WarpRing ring{bt_ring + size_t(warp) * RING_STAGES * TRIP_BYTES, bt_full[warp], 0};
   if (lane == 0) {
     for (int s = 0; s < RING_STAGES; ++s) mbar_init(&ring.full[s], 1);
@@ -240,6 +244,35 @@ static int launch_batched_k(const DeviceState& st, const BatchedArgs& a, cudaStr
   kern<<<grid, BT_THREADS, BT_RING_SMEM, stream>>>(a);
   note_launch();
   const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? POSPOPCNT_OK : cuda_fail(e);
+}
+
+// Offsets check (checked batched form): offsets[0] >= 0, nondecreasing,
+// offsets[nseg] <= n_words.  Any violation sets q->bad and the error word.
+__global__ void offsets_check_kernel(const int64_t* offsets, uint64_t nseg, uint64_t n_words, QueueSlot* q,
+                                     unsigned* err) {
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  bool bad = false;
+  for (uint64_t s = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < nseg; s += stride)
+    bad |= offsets[s] > offsets[s + 1];
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    bad |= offsets[0] < 0 || uint64_t(offsets[nseg]) > n_words || offsets[nseg] < 0;
+  if (__any_sync(FULL_MASK, bad) && (threadIdx.x & 31) == 0) {
+    atomicExch(&q->bad, 1u);
+    atomicOr(err, ERR_BIT_BAD_OFFSETS);
+  }
+}
+
+int launch_offsets_check(const DeviceState& st, const int64_t* d_offsets, size_t nseg, uint64_t n_words,
+                         void* queue_slot, cudaStream_t stream) {
+  QueueSlot* q = static_cast<QueueSlot*>(queue_slot);
+  cudaError_t e = cudaMemsetAsync(&q->bad, 0, sizeof(unsigned), stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  const uint64_t blocks = std::min<uint64_t>((nseg + 255) / 256, uint64_t(st.sms) * 8);
+  offsets_check_kernel<<<unsigned(std::max<uint64_t>(blocks, 1)), 256, 0, stream>>>(d_offsets, nseg, n_words, q,
+                                                                                     st.d_err);
+  note_launch();
+  e = cudaGetLastError();
   return e == cudaSuccess ? POSPOPCNT_OK : cuda_fail(e);
 }
 

@@ -286,7 +286,12 @@ __device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, uint32
 }
 
 // Error bits written to the library's device error word.
-enum : unsigned { ERR_BIT_TIMEOUT_FULL = 1u, ERR_BIT_TIMEOUT_EMPTY = 2u, ERR_BIT_TIMEOUT_DRAIN = 4u };
+enum : unsigned {
+  ERR_BIT_TIMEOUT_FULL = 1u,
+  ERR_BIT_TIMEOUT_EMPTY = 2u,
+  ERR_BIT_TIMEOUT_DRAIN = 4u,
+  ERR_BIT_BAD_OFFSETS = 8u
+};
 
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s per wait
 

@@ -68,6 +68,11 @@ int launch_batched(const DeviceState& st, const void* d_in, const int64_t* d_off
                    int width, unsigned long long* d_counts, void* queue_slot, int tile_words,
                    cudaStream_t stream, const uint64_t* d_seg_addr = nullptr);
 
+// Checks offsets on the device before a batched launch on the same slot:
+// a violation makes that launch count nothing and sets the error word.
+int launch_offsets_check(const DeviceState& st, const int64_t* d_offsets, size_t nseg, uint64_t n_words,
+                         void* queue_slot, cudaStream_t stream);
+
 // Monotonic host clock in seconds.
 double now_seconds();
 

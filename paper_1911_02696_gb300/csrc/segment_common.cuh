@@ -13,6 +13,7 @@ namespace ppc {
 struct QueueSlot {
   unsigned long long next;  // next tile index to hand out
   unsigned int done;        // CTAs that have finished
+  unsigned int bad;         // set by the offsets check: the launch counts nothing
 };
 
 constexpr int BT_THREADS = 256;
@@ -50,6 +51,7 @@ __device__ __forceinline__ void retire_cta(QueueSlot* q) {
     if (prev == gridDim.x - 1) {
       atomicExch(&q->next, 0ull);
       atomicExch(&q->done, 0u);
+      atomicExch(&q->bad, 0u);
       __threadfence();
     }
   }

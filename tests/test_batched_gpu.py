@@ -134,3 +134,37 @@ def test_full_20k_segments_one_hot():
     words = synth.segmented_one_hot(0, off, 16)
     got = _check(16, words, off)
     assert np.array_equal(got.sum(axis=1), lens.astype(np.uint64))
+
+
+def test_checked_form_valid_and_invalid_offsets():
+    """pospopcnt_batched_checked counts valid offsets like pospopcnt_batched
+    and turns offsets beyond the buffer or decreasing into an error status
+    (nothing counted, no access outside the input); the next call on the
+    same stream works again."""
+    rng = np.random.default_rng(8)
+    off = _layout(rng, 300, 5000, start=2)
+    words = synth.uniform_bits(8, int(off[-1]), 16)
+    _, x = _dev(words, 4)
+    d_off = torch.from_numpy(off).cuda()
+    assert ppc.pospopcnt_check_device_error() == 0
+    got = ppc.pospopcnt_batched_checked(x, d_off, 16)
+    assert ppc.pospopcnt_check_device_error() == 0
+    assert np.array_equal(got.cpu().numpy().view(np.uint64), oracle.pospopcnt_segments(words, off, 16))
+    beyond = off.copy()
+    beyond[-1] += 1000  # past the end of x
+    dec = off.copy()
+    dec[5], dec[6] = dec[6] + 1, dec[5]  # not monotone
+    neg = off.copy()
+    neg[0] = -1
+    for bad in (beyond, dec, neg):
+        out = torch.full((300, 16), 7, dtype=torch.int64, device="cuda")
+        ppc.pospopcnt_batched_checked(x, torch.from_numpy(bad).cuda(), 16, counts=out)
+        assert ppc.pospopcnt_check_device_error() == 1
+        assert torch.all(out == 0)
+    # the slot is clean again: unchecked and checked calls both count
+    got = ppc.pospopcnt_batched(x, d_off, 16)
+    got2 = ppc.pospopcnt_batched_checked(x, d_off, 16)
+    assert ppc.pospopcnt_check_device_error() == 0
+    ref = oracle.pospopcnt_segments(words, off, 16)
+    assert np.array_equal(got.cpu().numpy().view(np.uint64), ref)
+    assert np.array_equal(got2.cpu().numpy().view(np.uint64), ref)
