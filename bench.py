@@ -589,7 +589,8 @@ def run_serve(args, world, rank, local):
         srv = ppc.pospopcnt_server_create(local, hbm_budget_bytes=64 << 30, per_request=per_request,
                                           max_inflight=args.serve_slots_plain if per_request else args.serve_slots,
                                           max_batch_jobs=1 if per_request else 240,
-                                          large_job_bytes=int(args.serve_large_mib * (1 << 20)))
+                                          large_job_bytes=int(args.serve_large_mib * (1 << 20)),
+                                          max_large_inflight=0 if per_request else args.serve_large_inflight)
         try:
             # warm-up: a short slice of the trace
             k = min(n, 2000)
@@ -636,7 +637,7 @@ def run_serve(args, world, rank, local):
                        "requests": int(n), "total_GB": round(total / 1e9, 2),
                        "offered_GBps": round(total / args.serve_seconds / 1e9, 1),
                        "batched_slots": args.serve_slots, "per_request_slots": args.serve_slots_plain,
-                       "large_job_MiB": args.serve_large_mib},
+                       "large_job_MiB": args.serve_large_mib, "max_large_inflight": args.serve_large_inflight},
             "continuous_batching": batched, "per_request_plain": plain,
             "p99_speedup_vs_per_request": round(plain["p99_ms"] / batched["p99_ms"], 2),
             "results_same_alone_and_in_mix": same, "batched_equals_per_request_all": same_all}
@@ -731,6 +732,8 @@ def main(argv=None):
     p.add_argument("--serve-slots-plain", type=int, default=64, help="requests in flight (per-request mode)")
     p.add_argument("--serve-large-mib", type=float, default=4.0,
                    help="jobs at least this large are launched on their own")
+    p.add_argument("--serve-large-inflight", type=int, default=0,
+                   help="large jobs on the GPU at once in continuous batching (0: no limit)")
     p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--kernel", choices=["csa", "tma", "ballot"], default=None,
                    help="time one kernel family instead of the tuned default")

@@ -225,6 +225,8 @@ typedef struct {
   int max_batch_jobs;        /* jobs per batch, 1..240 (0: 240; per_request: 1) */
   int per_request;           /* 1: one plain launch per job */
   uint64_t large_job_bytes;  /* jobs at least this large get their own plain launch (0: 4 MiB) */
+  int max_large_inflight;    /* such jobs on the GPU at once (0: no limit); a large job launched
+                                alone gets the whole HBM bandwidth instead of sharing it */
 } pospopcnt_server_config;
 
 typedef struct {

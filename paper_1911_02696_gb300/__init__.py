@@ -61,7 +61,7 @@ class ServerConfig(ctypes.Structure):
     """pospopcnt_server_config."""
     _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_int),
                 ("max_batch_jobs", ctypes.c_int), ("per_request", ctypes.c_int),
-                ("large_job_bytes", ctypes.c_uint64)]
+                ("large_job_bytes", ctypes.c_uint64), ("max_large_inflight", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -447,9 +447,11 @@ def pospopcnt_selftest_timeout(limit_ns: int = 1_000_000, stream=None, device=No
 # serving
 
 def pospopcnt_server_create(device: int = 0, hbm_budget_bytes: int = 0, max_inflight: int = 0,
-                            max_batch_jobs: int = 0, per_request: bool = False, large_job_bytes: int = 0) -> int:
+                            max_batch_jobs: int = 0, per_request: bool = False, large_job_bytes: int = 0,
+                            max_large_inflight: int = 0) -> int:
     """Creates a serving runtime (see the C header); returns its handle."""
-    cfg = ServerConfig(hbm_budget_bytes, max_inflight, max_batch_jobs, int(per_request), large_job_bytes)
+    cfg = ServerConfig(hbm_budget_bytes, max_inflight, max_batch_jobs, int(per_request), large_job_bytes,
+                       max_large_inflight)
     h = ctypes.c_void_p()
     _check(_lib().pospopcnt_server_create(device, ctypes.byref(cfg), ctypes.byref(h)), "pospopcnt_server_create")
     return h.value

@@ -191,6 +191,8 @@ struct Server {
   std::deque<Job> pending[3];   // small jobs, per width: batched
   std::deque<Job> pending_large;  // jobs of >= large_job_bytes: one plain launch each
   uint64_t large_job_bytes = 0;
+  int large_limit = 0;           // large jobs on the GPU at once (0: no limit)
+  int large_in_flight = 0;
   AdmissionPolicy adm;
   uint64_t admitted_jobs = 0;
 
@@ -280,6 +282,7 @@ struct Server {
         }
       }
       if (s.remaining == 0) {
+        if (s.single && !cfg.per_request) --large_in_flight;
         s.jobs.clear();
         s.busy = false;
         any = true;
@@ -332,7 +335,8 @@ struct Server {
     double t = 0;
     for (int w = 0; w < 3; ++w)
       if (!pending[w].empty() && (best < 0 || pending[w].front().t_arrival < t)) best = w, t = pending[w].front().t_arrival;
-    if (!pending_large.empty() && (best < 0 || pending_large.front().t_arrival < t)) best = 3;
+    const bool large_ok = large_limit <= 0 || large_in_flight < large_limit;
+    if (large_ok && !pending_large.empty() && (best < 0 || pending_large.front().t_arrival < t)) best = 3;
     return best;
   }
 
@@ -349,6 +353,7 @@ struct Server {
     std::deque<Job>& src = qi == 3 ? pending_large : pending[qi];
     const size_t take = qi == 3 ? 1 : std::min<size_t>(src.size(), size_t(cfg.max_batch_jobs));
     s.single = qi == 3;
+    if (s.single && !cfg.per_request) ++large_in_flight;
     const int width = s.single ? src.front().width : widths[qi];
     s.width = width;
     s.jobs.assign(src.begin(), src.begin() + long(take));
@@ -405,6 +410,7 @@ struct Server {
         if (!s.finished[i]) finish(s, i, nullptr, rc, td);
     }
     if (s.remaining == 0) {
+      if (s.single && !cfg.per_request) --large_in_flight;
       s.jobs.clear();
       s.busy = false;
     }
@@ -489,6 +495,7 @@ int pospopcnt_server_create(int device, const pospopcnt_server_config* cfg_in, p
   s.st = st;
   s.adm.budget = cfg.hbm_budget_bytes;
   s.large_job_bytes = cfg.large_job_bytes ? cfg.large_job_bytes : (uint64_t(4) << 20);
+  s.large_limit = cfg.max_large_inflight;
   const size_t rows_bytes = size_t(ppc::SERVE_MAX_JOBS) * 32 * sizeof(uint64_t);
   const size_t pieces_bytes = size_t(ppc::SERVE_MAX_JOBS) * sizeof(unsigned);
   const size_t pieces_pad = ((pieces_bytes + 255) / 256) * 256;
