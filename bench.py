@@ -194,6 +194,9 @@ def make_input(kind: str, seed: int, log2_words: int | None = None):
     """(host words, width, start offset in bytes, description)."""
     import synth
     if log2_words is not None:  # a smaller case of the same workload (profiling)
+        if kind == "popcount":
+            return (synth.uniform_bytes(seed, 1 << log2_words), 1, 0,
+                    f"array popcount of 2^{log2_words} uniform random bytes")
         width = {"u8": 8, "u32": 32, "u64": 64}.get(kind, 16)
         return (synth.uniform_bits(seed, 1 << log2_words, width), width, 0,
                 f"pospopcnt_u{width} n=2^{log2_words} uniform random bits")

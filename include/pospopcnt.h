@@ -12,7 +12,7 @@
  *   - Words are little-endian; bit p of a word is (w >> p) & 1, so
  *     counts[0] belongs to the least significant bit.
  *   - n counts WORDS, not bytes.  Offsets are in words relative to d_in.
- *   - d_in must be aligned to the word size (1, 2 or 4 bytes); any such
+ *   - d_in must be aligned to the word size (1, 2, 4 or 8 bytes); any such
  *     start is valid: words before the first 16-byte boundary and after the
  *     last whole 16-byte vector are counted one by one (§4.1 counts the
  *     residual that does not fill a SIMD block with the scalar routine).
@@ -20,9 +20,11 @@
  *     counters; the *_accumulate entry point keeps that form).  Counts are
  *     exact uint64 values; every result is bit-exact.
  *   - Entry points taking a cudaStream_t are asynchronous on that stream:
- *     they enqueue a memset and one kernel, copy nothing between host and
- *     device and never synchronise.  The caller owns every buffer; the
- *     library never frees, retains or writes d_in.
+ *     they enqueue at most a memset of the outputs and one counting kernel
+ *     (a count that fits one CTA stores its result without the memset; the
+ *     checked batched form adds a small offsets check), copy nothing between
+ *     host and device and never synchronise.  The caller owns every buffer;
+ *     the library never frees, retains or writes d_in.
  *   - The first call on a device allocates the library's per-device
  *     workspace (error word, work-queue slots); pospopcnt_init() does that
  *     up front, after which the asynchronous calls allocate nothing.
@@ -102,6 +104,22 @@ int pospopcnt_u32(const void* d_in, size_t n, uint64_t* d_counts, cudaStream_t s
  * the batched and serving forms take 8, 16 or 32. */
 int pospopcnt_u64(const void* d_in, size_t n, uint64_t* d_counts, cudaStream_t stream);
 
+/* pospopcnt_u8/u16/u32/u64 for width 8, 16, 32 or 64 with an explicit
+ * kernel family (pospopcnt_kernel; width 64: CSA or TMA). */
+int pospopcnt_count(int width, int kernel, const void* d_in, size_t n, uint64_t* d_counts,
+                    cudaStream_t stream);
+
+/* The same with an explicit launch configuration (validated; see
+ * pospopcnt_config). */
+int pospopcnt_count_config(int width, const pospopcnt_config* cfg, const void* d_in, size_t n,
+                           uint64_t* d_counts, cudaStream_t stream);
+
+/* Accumulate form, the paper's convention (§4, Fig. 6 adds into its
+ * counters): d_counts[p] += counts[p].  Nothing is zeroed, so a stream can
+ * be counted in chunks over several calls. */
+int pospopcnt_count_accumulate(int width, const void* d_in, size_t n, uint64_t* d_counts,
+                               cudaStream_t stream);
+
 /* Array popcount: the number of set bits in nbytes bytes at d_in, written
  * to *d_count (device memory, one uint64).  This is the single sum that the
  * positional count generalises (Abstract; the Harley-Seal popcount of §2):
@@ -119,22 +137,6 @@ int pospopcnt_popcount(const void* d_in, size_t nbytes, uint64_t* d_count, cudaS
  * Asynchronous on `stream`. */
 int pospopcnt_onehot_counts(const void* d_ids, size_t n, int id_bytes, int k, uint64_t* d_counts,
                             cudaStream_t stream);
-
-/* The same for width 8, 16 or 32 with an explicit kernel family
- * (pospopcnt_kernel). */
-int pospopcnt_count(int width, int kernel, const void* d_in, size_t n, uint64_t* d_counts,
-                    cudaStream_t stream);
-
-/* The same with an explicit launch configuration (validated; see
- * pospopcnt_config). */
-int pospopcnt_count_config(int width, const pospopcnt_config* cfg, const void* d_in, size_t n,
-                           uint64_t* d_counts, cudaStream_t stream);
-
-/* Accumulate form, the paper's convention (§4, Fig. 6 adds into its
- * counters): d_counts[p] += counts[p].  Nothing is zeroed, so a stream can
- * be counted in chunks over several calls. */
-int pospopcnt_count_accumulate(int width, const void* d_in, size_t n, uint64_t* d_counts,
-                               cudaStream_t stream);
 
 /* pospopcnt of HOST memory (n words at h_in); writes the width uint64
  * counts to h_counts (host memory).  Synchronous: returns when h_counts is
