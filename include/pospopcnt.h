@@ -166,6 +166,18 @@ int pospopcnt_host_is_mapped(const void* h_in, size_t nbytes);
 int pospopcnt_batched(const void* d_in, const int64_t* d_offsets, size_t nseg, int width,
                       uint64_t* d_counts, cudaStream_t stream);
 
+/* A pospopcnt_batched call (its memset and its kernel) captured once into
+ * an instantiated CUDA graph; each pospopcnt_graph_launch recounts the same
+ * buffers (their contents may change between launches) with a single graph
+ * launch on `stream`.  The graph owns a work-queue slot: launches of one
+ * graph must not overlap each other on the GPU.  create() allocates the
+ * library workspace if needed, then captures; it is synchronous. */
+typedef struct pospopcnt_graph pospopcnt_graph;
+int pospopcnt_batched_graph_create(const void* d_in, const int64_t* d_offsets, size_t nseg, int width,
+                                   uint64_t* d_counts, pospopcnt_graph** out);
+int pospopcnt_graph_launch(pospopcnt_graph* graph, cudaStream_t stream);
+int pospopcnt_graph_destroy(pospopcnt_graph* graph);
+
 /* pospopcnt_batched with the offsets checked on the device first: d_in
  * holds n_words words; unless offsets[0] >= 0, the offsets are
  * nondecreasing and offsets[nseg] <= n_words, nothing is counted (the rows

@@ -24,7 +24,8 @@ __all__ = [
     "PospopcntError", "load", "pospopcnt_init", "pospopcnt_u8", "pospopcnt_u16", "pospopcnt_u32", "pospopcnt_u64", "pospopcnt_popcount", "pospopcnt_onehot_counts",
     "pospopcnt_count", "pospopcnt_count_config", "pospopcnt_count_accumulate", "pospopcnt_count_host",
     "pospopcnt_host_is_mapped",
-    "pospopcnt_batched", "pospopcnt_batched_checked", "pospopcnt_batched_noalloc", "pospopcnt_plain_segments", "pospopcnt_check_device_error", "pospopcnt_plan_split",
+    "pospopcnt_batched", "pospopcnt_batched_checked", "pospopcnt_batched_noalloc",
+    "pospopcnt_batched_graph_create", "pospopcnt_graph_launch", "pospopcnt_graph_destroy", "pospopcnt_plain_segments", "pospopcnt_check_device_error", "pospopcnt_plan_split",
     "pospopcnt_get_config", "pospopcnt_set_config", "pospopcnt_autotune", "pospopcnt_strerror",
     "pospopcnt_last_cuda_error", "pospopcnt_launch_count", "pospopcnt_selftest_timeout", "KERNELS",
     "Config", "pospopcnt_server_create", "pospopcnt_server_destroy", "pospopcnt_server_submit",
@@ -123,6 +124,9 @@ def _declare(lib):
         "pospopcnt_plain_segments": (i32, [vp, vp, sz, i32, vp, vp]),
         "pospopcnt_batched_noalloc": (i32, [vp, vp, sz, i32, vp, vp]),
         "pospopcnt_batched_checked": (i32, [vp, sz, vp, sz, i32, vp, vp]),
+        "pospopcnt_batched_graph_create": (i32, [vp, vp, sz, i32, vp, P(vp)]),
+        "pospopcnt_graph_launch": (i32, [vp, vp]),
+        "pospopcnt_graph_destroy": (i32, [vp]),
         "pospopcnt_check_device_error": (i32, [vp]),
         "pospopcnt_plan_split": (i32, [i32, u64, sz, P(sz), P(sz), P(sz)]),
         "pospopcnt_get_config": (i32, [i32, sz, P(Config)]),
@@ -334,6 +338,32 @@ def pospopcnt_batched(x, offsets, width: int, counts=None, stream=None):
         _check(_lib().pospopcnt_batched(ptr, offsets.data_ptr(), nseg, width, out.data_ptr(),
                                         _stream_handle(stream, x.device)), "pospopcnt_batched")
     return out
+
+
+def pospopcnt_batched_graph_create(x, offsets, width: int, counts) -> int:
+    """Captures pospopcnt_batched on these buffers into a CUDA graph; returns
+    its handle (launch with pospopcnt_graph_launch)."""
+    torch = _torch()
+    ptr, _ = _words(x, width)
+    nseg = max(offsets.numel() - 1, 0)
+    out = _counts_out(counts, width, nseg, x.device)
+    h = ctypes.c_void_p()
+    with torch.cuda.device(x.device):
+        _check(_lib().pospopcnt_batched_graph_create(ptr, offsets.data_ptr(), nseg, width, out.data_ptr(),
+                                                     ctypes.byref(h)), "pospopcnt_batched_graph_create")
+    return h.value
+
+
+def pospopcnt_graph_launch(graph: int, stream=None, device=None) -> None:
+    torch = _torch()
+    device = device if device is not None else torch.cuda.current_device()
+    with torch.cuda.device(device):
+        _check(_lib().pospopcnt_graph_launch(ctypes.c_void_p(graph), _stream_handle(stream, device)),
+               "pospopcnt_graph_launch")
+
+
+def pospopcnt_graph_destroy(graph: int) -> None:
+    _check(_lib().pospopcnt_graph_destroy(ctypes.c_void_p(graph)), "pospopcnt_graph_destroy")
 
 
 def pospopcnt_batched_checked(x, offsets, width: int, counts=None, stream=None):

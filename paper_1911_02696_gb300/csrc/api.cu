@@ -496,6 +496,56 @@ int pospopcnt_plain_segments(const void* d_in, const int64_t* h_offsets, size_t 
   return POSPOPCNT_OK;
 }
 
+}  // extern "C"
+
+struct pospopcnt_graph {
+  cudaStream_t stream = nullptr;  // the capture stream: its queue slot belongs to the graph
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+int pospopcnt_batched_graph_create(const void* d_in, const int64_t* d_offsets, size_t nseg, int width,
+                                   uint64_t* d_counts, pospopcnt_graph** out) {
+  if (!out) return POSPOPCNT_ERR_INVALID;
+  *out = nullptr;
+  int rc = POSPOPCNT_OK;
+  if (!current_state(&rc)) return rc;  // workspace first: nothing is allocated during capture
+  auto* g = new pospopcnt_graph();
+  cudaError_t e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    rc = cuda_fail(e);
+  } else {
+    rc = pospopcnt_batched(d_in, d_offsets, nseg, width, d_counts, g->stream);
+    const cudaError_t e2 = cudaStreamEndCapture(g->stream, &g->graph);
+    if (rc == POSPOPCNT_OK && e2 != cudaSuccess) rc = cuda_fail(e2);
+    if (rc == POSPOPCNT_OK && (e = cudaGraphInstantiate(&g->exec, g->graph, 0)) != cudaSuccess) rc = cuda_fail(e);
+  }
+  if (rc != POSPOPCNT_OK) {
+    pospopcnt_graph_destroy(g);
+    return rc;
+  }
+  *out = g;
+  return POSPOPCNT_OK;
+}
+
+int pospopcnt_graph_launch(pospopcnt_graph* g, cudaStream_t stream) {
+  if (!g || !g->exec) return POSPOPCNT_ERR_INVALID;
+  const cudaError_t e = cudaGraphLaunch(g->exec, stream);
+  return e == cudaSuccess ? POSPOPCNT_OK : cuda_fail(e);
+}
+
+int pospopcnt_graph_destroy(pospopcnt_graph* g) {
+  if (!g) return POSPOPCNT_ERR_INVALID;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  if (g->stream) cudaStreamDestroy(g->stream);
+  delete g;
+  return POSPOPCNT_OK;
+}
+
 int pospopcnt_check_device_error(cudaStream_t stream) {
   int rc = POSPOPCNT_OK;
   DeviceState* st = current_state(&rc);

@@ -27,20 +27,15 @@
 
 namespace ppc {
 
-// Segment s is words [offsets[s], offsets[s+1]) of a virtual word space.
-// Offsets form (seg_addr == nullptr): virtual word v is word v of `base`.
-// Descriptor form: segment s starts at byte address seg_addr[s], so virtual
-// word v of segment s is at seg_addr[s] + (v - offsets[s]) * k/8; segments
-// may then lie anywhere in device memory (the serving path).
+// Segment s is words [offsets[s], offsets[s+1]) of `base`.
 struct BatchedArgs {
   const uint8_t* base;
   const int64_t* offsets;
   uint64_t nseg;
   unsigned long long* counts;
   QueueSlot* q;
-  uint64_t tile_words;        // multiple of 8 warps x 16 bytes
-  const uint64_t* seg_addr;  // nullptr: offsets form
-  unsigned* err;             // device error word (bounded waits)
+  uint64_t tile_words;  // multiple of 8 warps x 16 bytes
+  unsigned* err;        // device error word (bounded waits)
 };
 
 // Per-warp bulk-copy ring: lane 0 streams the 16-byte-aligned body of a long
@@ -181,10 +176,9 @@ __global__ void __launch_bounds__(BT_THREADS, bt_batched_min_blocks<K>::value) b
   bool failed = false;
   const int64_t o0 = a.offsets[0];
   const int64_t oN = a.offsets[a.nseg];
-  // offsets form: units start at the 16-byte boundary at or before word o0,
-  // so inner unit boundaries are aligned; descriptor form: at o0
-  const uint64_t mis =
-      a.seg_addr ? 0 : (reinterpret_cast<uint64_t>(a.base) + uint64_t(o0) * WB) & 15;
+  // units start at the 16-byte boundary at or before word o0, so inner unit
+  // boundaries are aligned
+  const uint64_t mis = (reinterpret_cast<uint64_t>(a.base) + uint64_t(o0) * WB) & 15;
   const int64_t start = o0 - int64_t(mis / WB);
   const uint64_t U = a.tile_words;  // words per scheduling unit
   const uint64_t units = oN > start ? (uint64_t(oN - start) + U - 1) / U : 0;
@@ -217,9 +211,7 @@ __global__ void __launch_bounds__(BT_THREADS, bt_batched_min_blocks<K>::value) b
       const int64_t pa = seg_lo > w0 ? seg_lo : w0;
       const int64_t pb = seg_hi < w1 ? seg_hi : w1;
       if (pa < pb) {
-        const uint8_t* pbase =
-            a.seg_addr ? reinterpret_cast<const uint8_t*>(a.seg_addr[s] - uint64_t(seg_lo) * WB) : a.base;
-        if (!warp_count_piece<K>(pbase, uint64_t(pa), uint64_t(pb), a.counts + s * K, ring, a.err)) {
+        if (!warp_count_piece<K>(a.base, uint64_t(pa), uint64_t(pb), a.counts + s * K, ring, a.err)) {
           failed = true;
           break;
         }
@@ -235,8 +227,7 @@ __global__ void __launch_bounds__(BT_THREADS, bt_batched_min_blocks<K>::value) b
 template <int K>
 static int launch_batched_k(const DeviceState& st, const BatchedArgs& a, cudaStream_t stream) {
   auto kern = batched_kernel<K>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(BT_RING_SMEM)) != cudaSuccess)
-    return cuda_fail(cudaGetLastError());
+  if (const cudaError_t e = ensure_dynamic_smem(kern, st.device, int(BT_RING_SMEM))) return cuda_fail(e);
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, BT_THREADS, BT_RING_SMEM) != cudaSuccess || occ < 1)
     occ = 1;
@@ -278,9 +269,8 @@ int launch_offsets_check(const DeviceState& st, const int64_t* d_offsets, size_t
 
 int launch_batched(const DeviceState& st, const void* d_in, const int64_t* d_offsets, size_t nseg,
                    int width, unsigned long long* d_counts, void* queue_slot, int tile_words,
-                   cudaStream_t stream, const uint64_t* d_seg_addr) {
+                   cudaStream_t stream) {
   BatchedArgs a;
-  a.seg_addr = d_seg_addr;
   a.base = static_cast<const uint8_t*>(d_in);
   a.offsets = d_offsets;
   a.nseg = nseg;
@@ -373,8 +363,8 @@ extern "C" int pospopcnt_batched_noalloc(const void* d_in, const int64_t* d_offs
     return cuda_fail(e);
   DeviceState st;
   st.sms = sms;
+  st.device = dev;
   BatchedArgs a;
-  a.seg_addr = nullptr;
   a.base = static_cast<const uint8_t*>(d_in);
   a.offsets = d_offsets;
   a.nseg = nseg;

@@ -60,18 +60,28 @@ int launch_plain_sysmem(const DeviceState& st, int width, const void* d_in, size
 // Validates a configuration for a width; fills defaults for zero fields.
 int normalize_config(const DeviceState& st, int width, pospopcnt_config* cfg);
 
-// Launch of the batched kernel (counts zeroed by the caller).  With
-// d_seg_addr (nseg byte addresses) the segments are [d_offsets[s],
-// d_offsets[s+1]) of a virtual word space and segment s starts at
-// d_seg_addr[s]; d_in is then unused.
+// Launch of the batched kernel (counts zeroed by the caller).
 int launch_batched(const DeviceState& st, const void* d_in, const int64_t* d_offsets, size_t nseg,
                    int width, unsigned long long* d_counts, void* queue_slot, int tile_words,
-                   cudaStream_t stream, const uint64_t* d_seg_addr = nullptr);
+                   cudaStream_t stream);
 
 // Checks offsets on the device before a batched launch on the same slot:
 // a violation makes that launch count nothing and sets the error word.
 int launch_offsets_check(const DeviceState& st, const int64_t* d_offsets, size_t nseg, uint64_t n_words,
                          void* queue_slot, cudaStream_t stream);
+
+// Raises a kernel's dynamic shared-memory limit to `bytes` on the current
+// device once (cached per kernel instance and device), so later launches --
+// including launches captured into a CUDA graph -- make no attribute call.
+template <typename Kern>
+cudaError_t ensure_dynamic_smem(Kern kern, int device, int bytes) {
+  static int done[64] = {};  // largest limit already set, per device
+  if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+  if (done[device] >= bytes) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done[device] = bytes;
+  return e;
+}
 
 // Monotonic host clock in seconds.
 double now_seconds();

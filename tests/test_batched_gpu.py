@@ -168,3 +168,25 @@ def test_checked_form_valid_and_invalid_offsets():
     ref = oracle.pospopcnt_segments(words, off, 16)
     assert np.array_equal(got.cpu().numpy().view(np.uint64), ref)
     assert np.array_equal(got2.cpu().numpy().view(np.uint64), ref)
+
+
+def test_native_graph_api():
+    """pospopcnt_batched_graph_create captures once; every launch recounts
+    the current contents of the same buffers."""
+    rng = np.random.default_rng(9)
+    off = _layout(rng, 400, 30000, start=1)
+    _, x = _dev(synth.uniform_bits(0, int(off[-1]), 16), 2)
+    d_off = torch.from_numpy(off).cuda()
+    out = torch.empty((400, 16), dtype=torch.int64, device="cuda")
+    g = ppc.pospopcnt_batched_graph_create(x, d_off, 16, out)
+    try:
+        for seed in (1, 2, 3):
+            words = synth.uniform_bits(seed, int(off[-1]), 16)
+            x.copy_(torch.from_numpy(words.view(np.uint8)))
+            out.fill_(-1)
+            torch.cuda.synchronize()
+            ppc.pospopcnt_graph_launch(g)
+            torch.cuda.synchronize()
+            assert np.array_equal(out.cpu().numpy().view(np.uint64), oracle.pospopcnt_segments(words, off, 16))
+    finally:
+        ppc.pospopcnt_graph_destroy(g)
