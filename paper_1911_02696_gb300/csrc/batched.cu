@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(BT_THREADS, bt_batched_min_blocks<K>::value) b
 template <int K>
 static int launch_batched_k(const DeviceState& st, const BatchedArgs& a, cudaStream_t stream) {
   auto kern = batched_kernel<K>;
-  if (const cudaError_t e = ensure_dynamic_smem(kern, st.device, int(BT_RING_SMEM))) return cuda_fail(e);
+  if (const cudaError_t e = ensure_dynamic_smem<batched_kernel<K>>(st.device, int(BT_RING_SMEM))) return cuda_fail(e);
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, BT_THREADS, BT_RING_SMEM) != cudaSuccess || occ < 1)
     occ = 1;

@@ -70,15 +70,17 @@ int launch_batched(const DeviceState& st, const void* d_in, const int64_t* d_off
 int launch_offsets_check(const DeviceState& st, const int64_t* d_offsets, size_t nseg, uint64_t n_words,
                          void* queue_slot, cudaStream_t stream);
 
-// Raises a kernel's dynamic shared-memory limit to `bytes` on the current
-// device once (cached per kernel instance and device), so later launches --
-// including launches captured into a CUDA graph -- make no attribute call.
-template <typename Kern>
-cudaError_t ensure_dynamic_smem(Kern kern, int device, int bytes) {
+// Raises kernel Kern's dynamic shared-memory limit to `bytes` on the
+// current device once (one cache per kernel -- the template argument is the
+// kernel itself, not its type, which instances of one template share -- and
+// per device), so later launches, including launches captured into a CUDA
+// graph, make no attribute call.
+template <auto Kern>
+cudaError_t ensure_dynamic_smem(int device, int bytes) {
   static int done[64] = {};  // largest limit already set, per device
   if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
   if (done[device] >= bytes) return cudaSuccess;
-  const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  const cudaError_t e = cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess) done[device] = bytes;
   return e;
 }

@@ -393,7 +393,7 @@ static int launch_tma(const DeviceState& st, const PlainArgs& p, int bps, int st
                       cudaStream_t stream, int flags = 0) {
   auto kern = tma_kernel<K>;
   const size_t smem = size_t(stages) * size_t(chunk);
-  if (const cudaError_t e = ensure_dynamic_smem(kern, st.device, int(smem))) return cuda_fail(e);
+  if (const cudaError_t e = ensure_dynamic_smem<tma_kernel<K>>(st.device, int(smem))) return cuda_fail(e);
   TmaArgs a;
   a.p = p;
   a.body_bytes_ptr = reinterpret_cast<const uint8_t*>(p.body);
