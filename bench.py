@@ -341,7 +341,9 @@ def run_plain(args, world, rank, local):
             "config": {"workload": desc, "n_words": int(words.size), "width": width, "start_offset_bytes": offset,
                        "bytes_per_rank_step": nbytes, "launch_config": cfg, "parallelism": f"replicas x{world}",
                        "l2": f"input {nbytes / 2**20:.0f} MiB vs L2 126 MB: "
-                             + ("no flush needed" if nbytes > (256 << 20) else "L2-resident (profiling case)")},
+                             + ("more than twice L2, no flush needed" if nbytes > 2 * 126_000_000 else
+                                "larger than L2, partly re-read from L2" if nbytes > 126_000_000 else
+                                "L2-resident (small case)")},
             "words_per_s": round(value * 1e9 / max(1, width // 8), 1),
             "pct_hbm_peak": round(100 * value / world / peak, 2),
             "roofline": roofline,
