@@ -197,6 +197,9 @@ def make_input(kind: str, seed: int, log2_words: int | None = None):
         if kind == "popcount":
             return (synth.uniform_bytes(seed, 1 << log2_words), 1, 0,
                     f"array popcount of 2^{log2_words} uniform random bytes")
+        if kind == "onehot":
+            return (synth.categorical_ids(seed, 1 << log2_words, synth.zipf_cdf(16), np.uint8), -16, 0,
+                    f"fused one-hot encode + count: 2^{log2_words} u8 ids, Zipf(1.1) over 16 categories")
         width = {"u8": 8, "u32": 32, "u64": 64}.get(kind, 16)
         return (synth.uniform_bits(seed, 1 << log2_words, width), width, 0,
                 f"pospopcnt_u{width} n=2^{log2_words} uniform random bits")
@@ -317,17 +320,21 @@ def run_plain(args, world, rank, local):
 
     peak, peak_src = peak_hbm()
     launch_ms = statistics.mean(per_step)
-    achieved = (nbytes + width * 8) / (launch_ms * 1e-3) / 1e9
+    counts_bytes = (onehot_k or width) * 8
+    achieved = (nbytes + counts_bytes) / (launch_ms * 1e-3) / 1e9
     cfg = ppc.pospopcnt_get_config(16 if width == 1 else width, words.size // (2 if width == 1 else 1))
     if args.kernel:
         cfg = {"kernel": ppc.KERNELS[args.kernel], "note": "library default launch for this family"}
     kname = {1: "csa", 2: "tma", 3: "ballot"}[cfg["kernel"]]
+    kernel_label = f"{kname}_kernel<{width}>"
     if onehot_k:
         cfg, kname = {"kernel": "onehot", "k": onehot_k}, "onehot"
+        lw = 8 if onehot_k <= 8 else 16 if onehot_k <= 16 else 32
+        kernel_label = f"onehot_lut_kernel<{lw}> (8-bit ids, k = {onehot_k})"
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_source": f"{peak_src} (copy bandwidth)",
                 "traffic": profiled_traffic(f"{kname}_u{width}", nbytes),
-                "kernel": f"{kname}_kernel<{width}> (+ a {width * 8}-byte memset)"}
+                "kernel": f"{kernel_label} (+ a {counts_bytes}-byte memset)"}
     out = None
     if rank == 0:
         out = {

@@ -7,7 +7,9 @@
 // the one-hot words directly in registers -- with lanes of LW = 8, 16 or 32
 // bits (the smallest that holds k positions), 32/LW ids share one 32-bit
 // register -- and feeds those registers through the same carry-save circuit
-// F_4 and popc flush as the plain count.  Ids >= k encode to the empty word.
+// and popc flush as the plain count.  Ids >= k encode to the empty word.
+// 16- and 32-bit ids are encoded by a clamped shift and a mask (circuit F_4);
+// 8-bit ids by a lookup in shared memory (circuit F_5, or F_4 for 8-bit lanes).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,6 +29,7 @@ struct OnehotArgs {
   unsigned long long* counts;
   uint32_t k;
   uint32_t store;
+  uint32_t one;  // 1: multiplier of the FMA-pipe additions in the 8-bit-id kernel
 };
 
 // The j-th id of a 16-byte vector of IDB-byte ids (j known at compile time),
@@ -109,6 +112,232 @@ __global__ void __launch_bounds__(NTHREADS) onehot_kernel(OnehotArgs a) {
   block_reduce_add<LW, NTHREADS / 32>(c, a.counts, a.store != 0, int(k));
 }
 
+// 8-bit ids: the one-hot lane comes from a lookup table in shared memory
+// instead of a shift and a mask.  Row e of the table (256 bytes) holds, for
+// each of the 32 lanes of a warp, its own copy of two encodings of id e: at
+// byte 4*l the low-lane word lo(e), at byte 128 + 4*l the high-lane word
+// hi(e) (both zero for e >= k).  The 32 lookups of a warp thus fall in 32
+// different banks whatever the ids, and the byte offset of a lookup,
+// (id << 8) | (4 * lane), is one byte permute of the loaded word.
+//   LW = 32: lo(e) = 1 << e (one id per register);
+//   LW = 16: lo(e) = 1 << e, hi(e) = 1 << (e + 16): a register of two ids is
+//            lo(a) + hi(b);
+//   LW = 8:  lo(e) = 0x00010001 << e, hi(e) = 0x01000100 << e: lo(a) + hi(b)
+//            holds ids a, b in bytes 0, 1 (and again in 2, 3), and one byte
+//            permute of two such pairs gives the register of four ids.
+// The sums have disjoint bits, so they are integer multiply-adds by a runtime
+// 1 (OnehotArgs::one): they run on the FMA pipe, which is otherwise idle,
+// instead of the ALU pipe that the byte permutes and the circuit fill.
+constexpr int LUT_ROW = 256;
+constexpr int LUT_BYTES = 256 * LUT_ROW;  // 64 KiB
+
+template <int LW>
+__device__ __forceinline__ uint32_t lut_lo(uint32_t e, uint32_t k) {
+  if (e >= k) return 0u;
+  return LW == 8 ? 0x00010001u << e : 1u << e;
+}
+
+template <int LW>
+__device__ __forceinline__ uint32_t lut_hi(uint32_t e, uint32_t k) {
+  if (e >= k || LW == 32) return 0u;
+  return LW == 8 ? 0x01000100u << e : 1u << (e + 16);
+}
+
+// x * one + y on the FMA pipe (one == 1 at run time, unknown to the compiler).
+__device__ __forceinline__ uint32_t mad_one(uint32_t x, uint32_t one, uint32_t y) {
+  uint32_t d;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(x), "r"(one), "r"(y));
+  return d;
+}
+
+// Table reads.  With IMM != 0 the table's shared-window address is the
+// compile-time constant IMM and rides in the load instruction as its
+// immediate (no add per lookup); with IMM == 0 it is added at run time.
+template <uint32_t IMM>
+struct LutRef {
+  uint32_t base;  // shared-window address of the table
+  template <uint32_t D>
+  __device__ __forceinline__ uint32_t at(uint32_t off) const {
+    uint32_t v;
+    if constexpr (IMM != 0)
+      asm("ld.shared.u32 %0, [%1+%2];" : "=r"(v) : "r"(off), "n"(IMM + D));
+    else
+      asm("ld.shared.u32 %0, [%1+%2];" : "=r"(v) : "r"(off + base), "n"(D));
+    return v;
+  }
+};
+
+// Encoded registers of the 4 ids in word w (byte j = id j): LW = 32 gives 4
+// registers, 16 gives 2, 8 gives 1.
+template <int LW, uint32_t IMM>
+__device__ __forceinline__ void encode_word(uint32_t* r, uint32_t w, LutRef<IMM> t, uint32_t lanebase,
+                                            uint32_t one) {
+  uint32_t off[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) off[j] = __byte_perm(w, lanebase, 0x7604u | (unsigned(j) << 4));  // {4*lane, id j, 0, 0}
+  if constexpr (LW == 32) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) r[j] = t.template at<0>(off[j]);
+  } else if constexpr (LW == 16) {
+    r[0] = mad_one(t.template at<128>(off[1]), one, t.template at<0>(off[0]));
+    r[1] = mad_one(t.template at<128>(off[3]), one, t.template at<0>(off[2]));
+  } else {
+    const uint32_t p01 = mad_one(t.template at<128>(off[1]), one, t.template at<0>(off[0]));
+    const uint32_t p23 = mad_one(t.template at<128>(off[3]), one, t.template at<0>(off[2]));
+    r[0] = __byte_perm(p01, p23, 0x7610u);
+  }
+}
+
+// flush() with the additions on the FMA pipe.
+template <int K>
+__device__ __forceinline__ void flush_mad(uint32_t (&top)[K], uint32_t t, uint32_t one) {
+#pragma unroll
+  for (int p = 0; p < K; ++p) top[p] = mad_one(__popc(t & (lane_mask<K>::value << p)), one, top[p]);
+}
+
+// Circuit over 2^N registers per trip: F_5, or F_4 for 8-bit lanes (four
+// ids per register, so 16 registers already hold 64 ids).
+template <int LW>
+struct LutTrip {
+  static constexpr int REGS_PER_VEC = 16 / (32 / LW);  // 16 ids per vector
+  static constexpr int N = LW == 8 ? 4 : 5;
+  static constexpr int R = 1 << N;
+  static constexpr int U = R / REGS_PER_VEC;  // vectors per trip
+};
+
+// The thread's share of the body: whole trips, then at most one partial trip.
+template <int LW, int NTHREADS, uint32_t IMM>
+__device__ __forceinline__ void lut_count_body(const OnehotArgs& a, LutRef<IMM> t, uint32_t lanebase,
+                                               uint32_t (&top)[LW], uint32_t (&B)[LutTrip<LW>::N]) {
+  constexpr int REGS_PER_VEC = LutTrip<LW>::REGS_PER_VEC, N = LutTrip<LW>::N, R = LutTrip<LW>::R,
+                U = LutTrip<LW>::U;
+  const uint32_t one = a.one;
+  const uint64_t stride = uint64_t(gridDim.x) * NTHREADS;
+  const uint64_t span = uint64_t(U - 1) * stride;
+  uint64_t v = uint64_t(blockIdx.x) * NTHREADS + threadIdx.x;
+  // Whole trips (every vector present).  Each vector of the next trip is
+  // loaded into x[i] as soon as x[i] has been encoded, so the loads are in
+  // flight while the rest of the trip is encoded and counted.
+  uint4 x[U];
+  bool full = v + span < a.nvec;
+  if (full) {
+#pragma unroll
+    for (int i = 0; i < U; ++i) x[i] = ld_stream(a.body + v + i * stride);
+  }
+  while (full) {
+    const uint64_t vn = v + U * stride;
+    const bool full_n = vn + span < a.nvec;
+    uint32_t d[R];
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+      const uint32_t w[4] = {x[i].x, x[i].y, x[i].z, x[i].w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        encode_word<LW, IMM>(d + i * REGS_PER_VEC + j * (REGS_PER_VEC / 4), w[j], t, lanebase, one);
+      if (full_n) x[i] = ld_stream(a.body + vn + i * stride);
+    }
+    flush_mad<LW>(top, Circuit<N>::run(d, B), one);
+    v = vn;
+    full = full_n;
+  }
+  if (v < a.nvec) {  // last, partial trip: a missing vector reads as ids 255, which encode to nothing
+    uint32_t d[R];
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+      const uint64_t idx = v + i * stride;
+      const uint4 y = idx < a.nvec ? ld_stream(a.body + idx) : make_uint4(~0u, ~0u, ~0u, ~0u);
+      const uint32_t w[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        encode_word<LW, IMM>(d + i * REGS_PER_VEC + j * (REGS_PER_VEC / 4), w[j], t, lanebase, one);
+    }
+    flush_mad<LW>(top, Circuit<N>::run(d, B), one);
+  }
+}
+
+// Shared-window address of dynamic shared memory in a kernel with no static
+// shared memory: the GPU reserves the first 1 KiB of every block's window.
+// The kernel checks it at run time and adds the address itself otherwise.
+constexpr uint32_t LUT_USUAL_BASE = 1024;
+
+template <int LW, int NTHREADS>
+__global__ void __launch_bounds__(NTHREADS, 3) onehot_lut_kernel(OnehotArgs a) {
+  extern __shared__ __align__(1024) uint8_t lut[];  // the only shared memory of this kernel
+  constexpr int N = LutTrip<LW>::N;
+  const uint32_t lane = threadIdx.x & 31u;
+  for (uint32_t e = threadIdx.x >> 5; e < 256u; e += NTHREADS / 32) {
+    *reinterpret_cast<uint32_t*>(lut + e * LUT_ROW + lane * 4u) = lut_lo<LW>(e, a.k);
+    *reinterpret_cast<uint32_t*>(lut + e * LUT_ROW + 128u + lane * 4u) = lut_hi<LW>(e, a.k);
+  }
+  __syncthreads();
+  // Every lookup depends on lanebase, made here, after the barrier, so no
+  // lookup can be scheduled before the table is complete.
+  uint32_t lanebase;
+  asm volatile("mov.u32 %0, %1;" : "=r"(lanebase) : "r"(lane * 4u));
+  const uint32_t base = static_cast<uint32_t>(__cvta_generic_to_shared(lut));
+  uint32_t B[N] = {};
+  uint32_t top[LW];
+#pragma unroll
+  for (int p = 0; p < LW; ++p) top[p] = 0;
+  if (base == LUT_USUAL_BASE)
+    lut_count_body<LW, NTHREADS, LUT_USUAL_BASE>(a, LutRef<LUT_USUAL_BASE>{base}, lanebase, top, B);
+  else
+    lut_count_body<LW, NTHREADS, 0>(a, LutRef<0>{base}, lanebase, top, B);
+  uint32_t c[LW];
+  finalize<LW, N>(c, top, B);
+  if (blockIdx.x == 0) {  // head and tail ids (fewer than 16 each), one by one
+    const unsigned t = threadIdx.x;
+    if (t < a.head_ids) {
+      const uint32_t id = a.head[t];
+      count_word<LW>(c, id < a.k ? 1u << id : 0u);
+    }
+    if (t >= 32 && t - 32 < a.tail_ids) {
+      const uint32_t id = a.tail[t - 32];
+      count_word<LW>(c, id < a.k ? 1u << id : 0u);
+    }
+  }
+  // Block reduction in the table's memory, which is free once every warp is
+  // past its last lookup; one atomic (or store) per position.
+  constexpr int NWARPS = NTHREADS / 32, SH = 5 - ilog2<LW>::value;
+  uint32_t* red = reinterpret_cast<uint32_t*>(lut);  // [NWARPS][LW]
+  const uint32_t vsum = warp_reduce_positions<LW>(c);
+  __syncthreads();
+  if ((lane & ((1u << SH) - 1u)) == 0) red[(threadIdx.x >> 5) * LW + (lane >> SH)] = vsum;
+  __syncthreads();
+  if (threadIdx.x < a.k) {
+    unsigned long long sum = 0;
+#pragma unroll
+    for (int w = 0; w < NWARPS; ++w) sum += red[w * LW + threadIdx.x];
+    if (a.store)
+      a.counts[threadIdx.x] = sum;
+    else if (sum)
+      atomicAdd(a.counts + threadIdx.x, sum);
+  }
+}
+
+template <int LW>
+static int launch_onehot_lut(const DeviceState& st, OnehotArgs a, cudaStream_t stream) {
+  constexpr int T = 256;
+  constexpr int U = LutTrip<LW>::U;
+  auto kern = onehot_lut_kernel<LW, T>;
+  if (const cudaError_t e = ensure_dynamic_smem<onehot_lut_kernel<LW, T>>(st.device, LUT_BYTES)) return cuda_fail(e);
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, T, LUT_BYTES) != cudaSuccess || occ < 1) occ = 1;
+  const uint64_t cap = uint64_t(st.sms) * uint64_t(occ);
+  const uint64_t need = (a.nvec + uint64_t(U) * T - 1) / (uint64_t(U) * T);
+  uint64_t grid = std::max<uint64_t>(1, std::min(cap, need));
+  grid = std::max<uint64_t>(grid, ((a.nvec * 16) >> 31) + 1);  // per-CTA u32 partials stay exact
+  a.store = grid == 1 ? 1u : 0u;
+  if (grid > 1) {
+    const cudaError_t e = cudaMemsetAsync(a.counts, 0, sizeof(unsigned long long) * a.k, stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  kern<<<unsigned(grid), T, LUT_BYTES, stream>>>(a);
+  note_launch();
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? POSPOPCNT_OK : cuda_fail(e);
+}
+
 template <int IDB, int LW>
 static int launch_onehot(const DeviceState& st, OnehotArgs a, cudaStream_t stream) {
   constexpr int T = 256;
@@ -133,9 +362,15 @@ static int launch_onehot(const DeviceState& st, OnehotArgs a, cudaStream_t strea
 
 template <int IDB>
 static int launch_onehot_idb(const DeviceState& st, const OnehotArgs& a, cudaStream_t stream) {
-  if (a.k <= 8) return launch_onehot<IDB, 8>(st, a, stream);
-  if (a.k <= 16) return launch_onehot<IDB, 16>(st, a, stream);
-  return launch_onehot<IDB, 32>(st, a, stream);
+  if constexpr (IDB == 1) {
+    if (a.k <= 8) return launch_onehot_lut<8>(st, a, stream);
+    if (a.k <= 16) return launch_onehot_lut<16>(st, a, stream);
+    return launch_onehot_lut<32>(st, a, stream);
+  } else {
+    if (a.k <= 8) return launch_onehot<IDB, 8>(st, a, stream);
+    if (a.k <= 16) return launch_onehot<IDB, 16>(st, a, stream);
+    return launch_onehot<IDB, 32>(st, a, stream);
+  }
 }
 
 }  // namespace ppc
@@ -163,6 +398,7 @@ extern "C" int pospopcnt_onehot_counts(const void* d_ids, size_t n, int id_bytes
   a.counts = reinterpret_cast<unsigned long long*>(d_counts);
   a.k = uint32_t(k);
   a.store = 0;
+  a.one = 1;
   if (n == 0) {
     const cudaError_t e = cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * size_t(k), stream);
     return e == cudaSuccess ? POSPOPCNT_OK : cuda_fail(e);

@@ -58,6 +58,17 @@ def test_ragged_large_and_skewed(idb):
             assert np.array_equal(_run(ids, k, off), oracle.onehot_counts(ids, k))
 
 
+@pytest.mark.parametrize("k", [1, 7, 8, 12, 16, 20, 32])
+def test_u8_every_id_value(k):
+    """8-bit ids over all 256 values (most of them >= k, each of which must
+    encode to nothing), at lengths that end a thread's run of vectors
+    anywhere inside its last trip."""
+    rng = np.random.default_rng(k)
+    for n in (16 * 256 * 8 - 16, 16 * 256 * 8 + 16, 3 * (1 << 20) + 5, (1 << 22) + 16 * 4 * 256 * 3 + 1):
+        ids = rng.integers(0, 256, size=n).astype(np.uint8)
+        assert np.array_equal(_run(ids, k, int(rng.integers(0, 16))), oracle.onehot_counts(ids, k)), n
+
+
 def test_rejects():
     x = torch.zeros(16, dtype=torch.uint8, device="cuda")
     for k in (0, 33):
