@@ -29,7 +29,8 @@ struct OnehotArgs {
   unsigned long long* counts;
   uint32_t k;
   uint32_t store;
-  uint32_t one;  // 1: multiplier of the FMA-pipe additions in the 8-bit-id kernel
+  uint32_t one;  // 1: multiplier of the FMA-pipe additions in the 8-bit-id kernels
+  unsigned* err;  // device error word (bounded waits of the ring kernel)
 };
 
 // The j-th id of a 16-byte vector of IDB-byte ids (j known at compile time),
@@ -195,6 +196,55 @@ __device__ __forceinline__ void flush_mad(uint32_t (&top)[K], uint32_t t, uint32
   for (int p = 0; p < K; ++p) top[p] = mad_one(__popc(t & (lane_mask<K>::value << p)), one, top[p]);
 }
 
+// Per-thread counts of the 8-bit-id kernels.  A trip's circuit F_N returns
+// its top register (weight 2^N).  Top registers of consecutive trips are
+// combined as a binary counter of carry-save adders: two of weight 2^N give
+// a sum bit B[N] and a carry of weight 2^(N+1); two such carries give B[N+1]
+// and a carry of weight 2^(N+2), which is flushed with popc.  The flush thus
+// runs once per four trips -- the circuit F_(N+2) without holding
+// 2^(N+2) registers at once.
+template <int LW, int N>
+struct PairedCounts {
+  uint32_t B[N + 2];   // B[l] at weight 2^l
+  uint32_t pend0 = 0;  // unpaired top register of a trip (weight 2^N)
+  uint32_t pend1 = 0;  // unpaired carry of a pair of trips (weight 2^(N+1))
+  uint32_t trips = 0;
+  uint32_t top[LW];    // units of 2^(N+2)
+  __device__ __forceinline__ PairedCounts() {
+#pragma unroll
+    for (int l = 0; l < N + 2; ++l) B[l] = 0;
+#pragma unroll
+    for (int p = 0; p < LW; ++p) top[p] = 0;
+  }
+  __device__ __forceinline__ void add_trip(const uint32_t* d, uint32_t one) {
+    const uint32_t t = Circuit<N>::run(d, B);
+    if ((trips & 1u) == 0) {
+      pend0 = t;
+    } else {
+      uint32_t h;
+      csa(h, B[N], B[N], pend0, t);
+      pend0 = 0;
+      if ((trips & 2u) == 0) {
+        pend1 = h;
+      } else {
+        uint32_t h2;
+        csa(h2, B[N + 1], B[N + 1], pend1, h);
+        pend1 = 0;
+        flush_mad<LW>(top, h2, one);
+      }
+    }
+    ++trips;
+  }
+  __device__ __forceinline__ void finish(uint32_t (&c)[LW]) const {
+    finalize<LW, N + 2>(c, top, B);  // top at 2^(N+2), B[l] at 2^l
+#pragma unroll
+    for (int p = 0; p < LW; ++p) {
+      const uint32_t m = lane_mask<LW>::value << p;
+      c[p] += (static_cast<uint32_t>(__popc(pend0 & m)) << N) + (static_cast<uint32_t>(__popc(pend1 & m)) << (N + 1));
+    }
+  }
+};
+
 // Circuit over 2^N registers per trip: F_5, or F_4 for 8-bit lanes (four
 // ids per register, so 16 registers already hold 64 ids).
 template <int LW>
@@ -208,9 +258,8 @@ struct LutTrip {
 // The thread's share of the body: whole trips, then at most one partial trip.
 template <int LW, int NTHREADS, uint32_t IMM>
 __device__ __forceinline__ void lut_count_body(const OnehotArgs& a, LutRef<IMM> t, uint32_t lanebase,
-                                               uint32_t (&top)[LW], uint32_t (&B)[LutTrip<LW>::N]) {
-  constexpr int REGS_PER_VEC = LutTrip<LW>::REGS_PER_VEC, N = LutTrip<LW>::N, R = LutTrip<LW>::R,
-                U = LutTrip<LW>::U;
+                                               PairedCounts<LW, LutTrip<LW>::N>& acc) {
+  constexpr int REGS_PER_VEC = LutTrip<LW>::REGS_PER_VEC, R = LutTrip<LW>::R, U = LutTrip<LW>::U;
   const uint32_t one = a.one;
   const uint64_t stride = uint64_t(gridDim.x) * NTHREADS;
   const uint64_t span = uint64_t(U - 1) * stride;
@@ -236,7 +285,7 @@ __device__ __forceinline__ void lut_count_body(const OnehotArgs& a, LutRef<IMM> 
         encode_word<LW, IMM>(d + i * REGS_PER_VEC + j * (REGS_PER_VEC / 4), w[j], t, lanebase, one);
       if (full_n) x[i] = ld_stream(a.body + vn + i * stride);
     }
-    flush_mad<LW>(top, Circuit<N>::run(d, B), one);
+    acc.add_trip(d, one);
     v = vn;
     full = full_n;
   }
@@ -251,7 +300,7 @@ __device__ __forceinline__ void lut_count_body(const OnehotArgs& a, LutRef<IMM> 
       for (int j = 0; j < 4; ++j)
         encode_word<LW, IMM>(d + i * REGS_PER_VEC + j * (REGS_PER_VEC / 4), w[j], t, lanebase, one);
     }
-    flush_mad<LW>(top, Circuit<N>::run(d, B), one);
+    acc.add_trip(d, one);
   }
 }
 
@@ -275,16 +324,13 @@ __global__ void __launch_bounds__(NTHREADS, 3) onehot_lut_kernel(OnehotArgs a) {
   uint32_t lanebase;
   asm volatile("mov.u32 %0, %1;" : "=r"(lanebase) : "r"(lane * 4u));
   const uint32_t base = static_cast<uint32_t>(__cvta_generic_to_shared(lut));
-  uint32_t B[N] = {};
-  uint32_t top[LW];
-#pragma unroll
-  for (int p = 0; p < LW; ++p) top[p] = 0;
+  PairedCounts<LW, N> acc;
   if (base == LUT_USUAL_BASE)
-    lut_count_body<LW, NTHREADS, LUT_USUAL_BASE>(a, LutRef<LUT_USUAL_BASE>{base}, lanebase, top, B);
+    lut_count_body<LW, NTHREADS, LUT_USUAL_BASE>(a, LutRef<LUT_USUAL_BASE>{base}, lanebase, acc);
   else
-    lut_count_body<LW, NTHREADS, 0>(a, LutRef<0>{base}, lanebase, top, B);
+    lut_count_body<LW, NTHREADS, 0>(a, LutRef<0>{base}, lanebase, acc);
   uint32_t c[LW];
-  finalize<LW, N>(c, top, B);
+  acc.finish(c);
   if (blockIdx.x == 0) {  // head and tail ids (fewer than 16 each), one by one
     const unsigned t = threadIdx.x;
     if (t < a.head_ids) {
@@ -338,6 +384,224 @@ static int launch_onehot_lut(const DeviceState& st, OnehotArgs a, cudaStream_t s
   return e == cudaSuccess ? POSPOPCNT_OK : cuda_fail(e);
 }
 
+// ---------------------------------------------------------------------------
+// Large inputs of 8-bit ids: the same encoding and circuit, with the ids
+// brought in by bulk copies.  One CTA per SM: one producer lane streams
+// 32 KiB chunks into a 4-stage ring (full/empty mbarriers, bounded waits),
+// 16 consumer warps read them back with 16-byte shared loads.  Up to 128 KiB
+// per SM is in flight without holding a register, and the 64 KiB table is
+// shared by 16 warps instead of 8.  Everything lives in dynamic shared
+// memory -- table, ring, barriers -- so the table keeps the usual address.
+constexpr int RING_CWARPS = 24;
+constexpr int RING_THREADS = (RING_CWARPS + 1) * 32;
+constexpr uint32_t RING_CHUNK = 49152;  // one trip of 4 vectors for each of the 768 consumer threads
+constexpr uint32_t RING_STAGES = 3;
+
+struct RingCtl {
+  uint64_t full[RING_STAGES];
+  uint64_t empty[RING_STAGES];
+  uint32_t issued;                 // chunks the producer issued
+  uint32_t abort;
+  uint32_t consumed[RING_CWARPS];  // chunks each consumer warp finished
+};
+
+constexpr size_t RING_SMEM = size_t(LUT_BYTES) + size_t(RING_STAGES) * RING_CHUNK + sizeof(RingCtl);
+static_assert(RING_CHUNK % (16 * 4 * RING_CWARPS * 32) == 0 && RING_CHUNK % (16 * 2 * RING_CWARPS * 32) == 0,
+              "a chunk is a whole number of consumer trips");
+constexpr uint64_t RING_MIN_BYTES = uint64_t(32) << 20;
+
+// One trip over vectors [base, base + U*CT) of a ring stage; GUARD: some may
+// lie past nv (the partial last chunk of the input) and read as ids 255.
+template <int LW, uint32_t IMM, bool GUARD>
+__device__ __forceinline__ void ring_trip(const uint4* sv, uint32_t base, uint32_t nv, LutRef<IMM> t,
+                                          uint32_t lanebase, uint32_t one, PairedCounts<LW, LutTrip<LW>::N>& acc) {
+  constexpr int REGS_PER_VEC = LutTrip<LW>::REGS_PER_VEC, R = LutTrip<LW>::R, U = LutTrip<LW>::U;
+  constexpr uint32_t CT = RING_CWARPS * 32;
+  uint32_t d[R];
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+    const uint32_t idx = base + j * CT + threadIdx.x;
+    const uint4 y = (!GUARD || idx < nv) ? sv[idx] : make_uint4(~0u, ~0u, ~0u, ~0u);
+    const uint32_t w[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      encode_word<LW, IMM>(d + j * REGS_PER_VEC + q * (REGS_PER_VEC / 4), w[q], t, lanebase, one);
+  }
+  acc.add_trip(d, one);
+}
+
+// The consumer warps' loop over this CTA's chunks; returns the chunks it
+// finished.  A wait that runs out sets the error word and ends the loop (the
+// producer's own bounded waits end it there).
+template <int LW, uint32_t IMM>
+__device__ __forceinline__ uint32_t ring_consume(const OnehotArgs& a, const uint8_t* ring, RingCtl* ctl,
+                                                 uint32_t my_chunks, LutRef<IMM> t, uint32_t lanebase,
+                                                 PairedCounts<LW, LutTrip<LW>::N>& acc) {
+  constexpr uint32_t TRIP = LutTrip<LW>::U * RING_CWARPS * 32;  // vectors per trip; divides a chunk
+  constexpr uint32_t CV = RING_CHUNK / 16;                       // vectors per chunk
+  const uint32_t one = a.one, lane = threadIdx.x & 31u;
+  // Only the input's last chunk can be partial; it is this CTA's last chunk
+  // if this CTA holds it.
+  const uint64_t body_bytes = a.nvec * 16;
+  const uint64_t nchunks = (body_bytes + RING_CHUNK - 1) / RING_CHUNK;
+  const bool last_partial = body_bytes % RING_CHUNK != 0 && (nchunks - 1) % gridDim.x == blockIdx.x;
+  const uint32_t full_chunks = last_partial ? my_chunks - 1 : my_chunks;
+  uint32_t i = 0, s = 0, parity = 0;
+  for (; i < my_chunks; ++i) {
+    // every lane waits (each acquires the copied bytes); the verdict is made
+    // warp-uniform so the warp leaves the loop together
+    if (!__all_sync(FULL_MASK, mbar_wait_bounded(&ctl->full[s], parity, WAIT_LIMIT_NS))) {
+      if (lane == 0) {
+        atomicOr(a.err, ERR_BIT_TIMEOUT_FULL);
+        atomicExch(&ctl->abort, 1u);
+      }
+      break;
+    }
+    const uint4* sv = reinterpret_cast<const uint4*>(ring + size_t(s) * RING_CHUNK);
+    if (i < full_chunks) {
+#pragma unroll
+      for (uint32_t base = 0; base < CV; base += TRIP)
+        ring_trip<LW, IMM, false>(sv, base, CV, t, lanebase, one, acc);
+    } else {
+      const uint32_t nv = uint32_t(body_bytes % RING_CHUNK) / 16u;
+      for (uint32_t base = 0; base < nv; base += TRIP) ring_trip<LW, IMM, true>(sv, base, nv, t, lanebase, one, acc);
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&ctl->empty[s]);
+    if (++s == RING_STAGES) {
+      s = 0;
+      parity ^= 1u;
+    }
+  }
+  return i;
+}
+
+template <int LW>
+__global__ void __launch_bounds__(RING_THREADS, 1) onehot_ring_kernel(OnehotArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem[];  // the only shared memory of this kernel
+  uint8_t* lut = smem;
+  const uint8_t* ring = smem + LUT_BYTES;
+  RingCtl* ctl = reinterpret_cast<RingCtl*>(smem + LUT_BYTES + size_t(RING_STAGES) * RING_CHUNK);
+  constexpr int N = LutTrip<LW>::N;
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  const uint64_t body_bytes = a.nvec * 16;
+  const uint64_t nchunks = (body_bytes + RING_CHUNK - 1) / RING_CHUNK;
+  const uint32_t my_chunks =
+      blockIdx.x < nchunks ? uint32_t((nchunks - 1 - blockIdx.x) / gridDim.x + 1) : 0u;
+
+  if (threadIdx.x == 0) {
+    for (uint32_t s = 0; s < RING_STAGES; ++s) {
+      mbar_init(&ctl->full[s], 1);
+      mbar_init(&ctl->empty[s], RING_CWARPS);
+    }
+    ctl->issued = 0;
+    ctl->abort = 0;
+    mbar_fence_init();
+  }
+  for (uint32_t e = warp; e < 256u; e += RING_CWARPS + 1) {
+    *reinterpret_cast<uint32_t*>(lut + e * LUT_ROW + lane * 4u) = lut_lo<LW>(e, a.k);
+    *reinterpret_cast<uint32_t*>(lut + e * LUT_ROW + 128u + lane * 4u) = lut_hi<LW>(e, a.k);
+  }
+  __syncthreads();
+
+  uint32_t c[LW];
+#pragma unroll
+  for (int p = 0; p < LW; ++p) c[p] = 0;
+  if (warp == RING_CWARPS) {
+    if (lane == 0) {  // producer: one lane issues every copy
+      uint32_t i = 0;
+      for (; i < my_chunks; ++i) {
+        const uint32_t s = i % RING_STAGES, use = i / RING_STAGES;
+        if (use > 0 && !mbar_wait_bounded(&ctl->empty[s], (use - 1) & 1u, WAIT_LIMIT_NS)) {
+          atomicOr(a.err, ERR_BIT_TIMEOUT_EMPTY);
+          atomicExch(&ctl->abort, 1u);
+          break;
+        }
+        if (*((volatile uint32_t*)&ctl->abort)) break;
+        const uint64_t off = (blockIdx.x + uint64_t(i) * gridDim.x) * RING_CHUNK;
+        const uint64_t rem = body_bytes - off;
+        const uint32_t bytes = rem < RING_CHUNK ? uint32_t(rem) : RING_CHUNK;
+        mbar_arrive_expect_tx(&ctl->full[s], bytes);
+        bulk_g2s(smem + LUT_BYTES + size_t(s) * RING_CHUNK, reinterpret_cast<const uint8_t*>(a.body) + off, bytes,
+                 &ctl->full[s]);
+      }
+      ctl->issued = i;
+    }
+  } else {
+    // Every lookup depends on lanebase, made after the barrier above.
+    uint32_t lanebase;
+    asm volatile("mov.u32 %0, %1;" : "=r"(lanebase) : "r"(lane * 4u));
+    const uint32_t base = static_cast<uint32_t>(__cvta_generic_to_shared(lut));
+    PairedCounts<LW, N> acc;
+    const uint32_t done =
+        base == LUT_USUAL_BASE
+            ? ring_consume<LW, LUT_USUAL_BASE>(a, ring, ctl, my_chunks, LutRef<LUT_USUAL_BASE>{base}, lanebase, acc)
+            : ring_consume<LW, 0>(a, ring, ctl, my_chunks, LutRef<0>{base}, lanebase, acc);
+    if (lane == 0) ctl->consumed[warp] = done;
+    acc.finish(c);
+  }
+  __syncthreads();
+  // After an abort, wait (bounded) for copies still in flight before the
+  // shared memory they target goes away.
+  if (ctl->abort && threadIdx.x == 0) {
+    uint32_t lo = ctl->issued;
+    for (int w = 0; w < RING_CWARPS; ++w) lo = ctl->consumed[w] < lo ? ctl->consumed[w] : lo;
+    for (uint32_t i = lo; i < ctl->issued; ++i) {
+      if (!mbar_wait_bounded(&ctl->full[i % RING_STAGES], (i / RING_STAGES) & 1u, WAIT_LIMIT_NS)) {
+        atomicOr(a.err, ERR_BIT_TIMEOUT_DRAIN);
+        break;
+      }
+    }
+  }
+  if (blockIdx.x == 0) {  // head and tail ids (fewer than 16 each), one by one
+    const unsigned t = threadIdx.x;
+    if (t < a.head_ids) {
+      const uint32_t id = a.head[t];
+      count_word<LW>(c, id < a.k ? 1u << id : 0u);
+    }
+    if (t >= 32 && t - 32 < a.tail_ids) {
+      const uint32_t id = a.tail[t - 32];
+      count_word<LW>(c, id < a.k ? 1u << id : 0u);
+    }
+  }
+  // Block reduction in the table's memory (no lookup is left after the
+  // barrier above); the producer warp holds no counts.
+  constexpr int SH = 5 - ilog2<LW>::value;
+  uint32_t* red = reinterpret_cast<uint32_t*>(lut);  // [RING_CWARPS][LW]
+  const uint32_t vsum = warp_reduce_positions<LW>(c);
+  if (warp < RING_CWARPS && (lane & ((1u << SH) - 1u)) == 0) red[warp * LW + (lane >> SH)] = vsum;
+  __syncthreads();
+  if (threadIdx.x < a.k) {
+    unsigned long long sum = 0;
+#pragma unroll
+    for (int w = 0; w < RING_CWARPS; ++w) sum += red[w * LW + threadIdx.x];
+    if (a.store)
+      a.counts[threadIdx.x] = sum;
+    else if (sum)
+      atomicAdd(a.counts + threadIdx.x, sum);
+  }
+}
+
+template <int LW>
+static int launch_onehot_ring(const DeviceState& st, OnehotArgs a, cudaStream_t stream) {
+  auto kern = onehot_ring_kernel<LW>;
+  if (const cudaError_t e = ensure_dynamic_smem<onehot_ring_kernel<LW>>(st.device, int(RING_SMEM)))
+    return cuda_fail(e);
+  const uint64_t nchunks = (a.nvec * 16 + RING_CHUNK - 1) / RING_CHUNK;
+  uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(uint64_t(st.sms), nchunks));
+  // a consumer warp's u32 partials stay exact: at most 2^31 ids per warp
+  grid = std::max(grid, std::min<uint64_t>(nchunks, ((a.nvec * 16) >> 35) + 1));
+  a.store = grid == 1 ? 1u : 0u;
+  if (grid > 1) {
+    const cudaError_t e = cudaMemsetAsync(a.counts, 0, sizeof(unsigned long long) * a.k, stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  kern<<<unsigned(grid), RING_THREADS, RING_SMEM, stream>>>(a);
+  note_launch();
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? POSPOPCNT_OK : cuda_fail(e);
+}
+
 template <int IDB, int LW>
 static int launch_onehot(const DeviceState& st, OnehotArgs a, cudaStream_t stream) {
   constexpr int T = 256;
@@ -363,6 +627,11 @@ static int launch_onehot(const DeviceState& st, OnehotArgs a, cudaStream_t strea
 template <int IDB>
 static int launch_onehot_idb(const DeviceState& st, const OnehotArgs& a, cudaStream_t stream) {
   if constexpr (IDB == 1) {
+    if (a.nvec * 16 >= RING_MIN_BYTES) {  // enough chunks to give every SM several
+      if (a.k <= 8) return launch_onehot_ring<8>(st, a, stream);
+      if (a.k <= 16) return launch_onehot_ring<16>(st, a, stream);
+      return launch_onehot_ring<32>(st, a, stream);
+    }
     if (a.k <= 8) return launch_onehot_lut<8>(st, a, stream);
     if (a.k <= 16) return launch_onehot_lut<16>(st, a, stream);
     return launch_onehot_lut<32>(st, a, stream);
@@ -399,6 +668,7 @@ extern "C" int pospopcnt_onehot_counts(const void* d_ids, size_t n, int id_bytes
   a.k = uint32_t(k);
   a.store = 0;
   a.one = 1;
+  a.err = st->d_err;
   if (n == 0) {
     const cudaError_t e = cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * size_t(k), stream);
     return e == cudaSuccess ? POSPOPCNT_OK : cuda_fail(e);

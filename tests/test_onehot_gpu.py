@@ -1,7 +1,8 @@
 """Fused one-hot encode + count on the GPU against the oracle (which one-hot
 encodes each id and then counts positions, §1): every id width, k on both
 sides of the 8/16/32-bit lane boundaries, ids >= k present, every small
-length at every aligned start, ragged large sizes, skewed ids, 2 GiB."""
+length at every aligned start, ragged large sizes, skewed ids, both 8-bit-id
+kernels (register loads below 32 MiB, bulk-copy ring above), 2 GiB."""
 import numpy as np
 import pytest
 
@@ -67,6 +68,20 @@ def test_u8_every_id_value(k):
     for n in (16 * 256 * 8 - 16, 16 * 256 * 8 + 16, 3 * (1 << 20) + 5, (1 << 22) + 16 * 4 * 256 * 3 + 1):
         ids = rng.integers(0, 256, size=n).astype(np.uint8)
         assert np.array_equal(_run(ids, k, int(rng.integers(0, 16))), oracle.onehot_counts(ids, k)), n
+
+
+@pytest.mark.parametrize("k", [3, 8, 16, 17, 32])
+def test_u8_bulk_copy_sizes(k):
+    """8-bit ids from 32 MiB up go through bulk copies into a shared-memory
+    ring: the exact threshold, a ragged chunk count, a partial last chunk
+    at an odd start, ids over all 256 values and skewed ids."""
+    rng = np.random.default_rng(100 + k)
+    sizes = [(32 << 20, 0), ((32 << 20) - 16, 0), (152 * 32768 * 7 + 16 * 100 + 3, 5), ((40 << 20) + 17, 3)]
+    for n, off in sizes:
+        ids = rng.integers(0, 256, size=n).astype(np.uint8)
+        assert np.array_equal(_run(ids, k, off), oracle.onehot_counts(ids, k)), (n, off)
+    ids = synth.categorical_ids(k, (48 << 20) + 9, synth.zipf_cdf(min(2 * k, 64)), np.uint8)
+    assert np.array_equal(_run(ids, k, 1), oracle.onehot_counts(ids, k))
 
 
 def test_rejects():
