@@ -75,7 +75,7 @@ def profiled_traffic(kernel_key: str, nbytes: int):
     except Exception:
         return None
     e = rec.get(kernel_key)
-    if not e or e.get("csrc_hash") != csrc_hash():
+    if not e or e.get("csrc_hash") != csrc_hash(tuple(e.get("sources", KERNEL_SOURCES))):
         return None
     # scale by input bytes (traffic grows in proportion for a streaming scan)
     return int(e["dram_bytes_per_launch"] * nbytes / e["input_bytes"])
@@ -330,7 +330,8 @@ def run_plain(args, world, rank, local):
     if onehot_k:
         cfg, kname = {"kernel": "onehot", "k": onehot_k}, "onehot"
         lw = 8 if onehot_k <= 8 else 16 if onehot_k <= 16 else 32
-        kernel_label = f"onehot_lut_kernel<{lw}> (8-bit ids, k = {onehot_k})"
+        kernel_label = (f"onehot_ring_kernel<{lw}>" if nbytes >= (32 << 20) else f"onehot_lut_kernel<{lw}, 256>") \
+            + f" (8-bit ids, k = {onehot_k})"
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_source": f"{peak_src} (copy bandwidth)",
                 "traffic": profiled_traffic(f"{kname}_u{width}", nbytes),
