@@ -24,6 +24,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -190,59 +191,104 @@ def whole_job_throughput(bytes_per_rank_step: int, steps: int, world: int, max_m
 # ---------------------------------------------------------------------------
 # workloads
 
-def make_input(kind: str, seed: int, log2_words: int | None = None):
-    """(host words, width, start offset in bytes, description)."""
+def make_input(kind: str, seed: int, log2_words: int | None = None, limit: int | None = None):
+    """(host words, width, start offset in bytes, description).  With `limit`
+    only the first `limit` words are made -- the same words as the first ones
+    of the full input, every generator being a function of (seed, index) --
+    while the description still names the full workload."""
     import synth
+    zipf16 = synth.zipf_cdf(16)
     if log2_words is not None:  # a smaller case of the same workload (profiling)
-        if kind == "popcount":
-            return (synth.uniform_bytes(seed, 1 << log2_words), 1, 0,
-                    f"array popcount of 2^{log2_words} uniform random bytes")
-        if kind == "onehot":
-            return (synth.categorical_ids(seed, 1 << log2_words, synth.zipf_cdf(16), np.uint8), -16, 0,
-                    f"fused one-hot encode + count: 2^{log2_words} u8 ids, Zipf(1.1) over 16 categories")
+        n = 1 << log2_words
+        table = {
+            "popcount": (1, f"array popcount of 2^{log2_words} uniform random bytes",
+                         lambda m: synth.uniform_bytes(seed, m)),
+            "onehot": (-16, f"fused one-hot encode + count: 2^{log2_words} u8 ids, Zipf(1.1) over 16 categories",
+                       lambda m: synth.categorical_ids(seed, m, zipf16, np.uint8)),
+        }
         width = {"u8": 8, "u32": 32, "u64": 64}.get(kind, 16)
-        return (synth.uniform_bits(seed, 1 << log2_words, width), width, 0,
-                f"pospopcnt_u{width} n=2^{log2_words} uniform random bits")
-    if kind == "u16":
-        return synth.uniform_bits(seed, 1 << 30, 16), 16, 0, "pospopcnt_u16 n=2^30 uniform random bits (2 GiB)"
-    if kind == "u16_onehot":
-        return synth.one_hot(seed, 1 << 30, 16), 16, 0, "pospopcnt_u16 n=2^30 one-hot Zipf(1.1) (2 GiB)"
-    if kind == "u16_sparse":
-        return synth.sparse(seed, 1 << 30, 16), 16, 0, "pospopcnt_u16 n=2^30 sparse Bernoulli(0.01) (2 GiB)"
-    if kind == "u16_misaligned":
-        return (synth.uniform_bits(seed, (1 << 30) + 7, 16), 16, 2,
-                "pospopcnt_u16 n=2^30+7 uniform bits, start 2 bytes past a 256-byte boundary")
-    if kind == "u8":
-        return synth.uniform_bits(seed, 1 << 31, 8), 8, 0, "pospopcnt_u8 n=2^31 uniform random bits (2 GiB)"
-    if kind == "onehot":
-        ids = synth.categorical_ids(seed, 1 << 31, synth.zipf_cdf(16), np.uint8)
-        return ids, -16, 0, "fused one-hot encode + count: 2^31 u8 ids, Zipf(1.1) over 16 categories (2 GiB)"
-    if kind == "popcount":
-        return synth.uniform_bytes(seed, 1 << 31), 1, 0, "array popcount of 2 GiB of uniform random bits"
-    if kind == "u64":
-        return synth.uniform_bits(seed, 1 << 28, 64), 64, 0, "pospopcnt_u64 n=2^28 uniform random bits (2 GiB)"
-    if kind == "u32":
-        return synth.uniform_bits(seed, 1 << 29, 32), 32, 0, "pospopcnt_u32 n=2^29 uniform random bits (2 GiB)"
-    raise ValueError(kind)
+        width, desc, gen = table.get(kind, (width, f"pospopcnt_u{width} n=2^{log2_words} uniform random bits",
+                                            lambda m: synth.uniform_bits(seed, m, width)))
+        return gen(min(n, limit or n)), width, 0, desc
+    table = {  # kind: (words, width, start offset in bytes, description, generator)
+        "u16": (1 << 30, 16, 0, "pospopcnt_u16 n=2^30 uniform random bits (2 GiB)",
+                lambda m: synth.uniform_bits(seed, m, 16)),
+        "u16_onehot": (1 << 30, 16, 0, "pospopcnt_u16 n=2^30 one-hot Zipf(1.1) (2 GiB)",
+                       lambda m: synth.one_hot(seed, m, 16)),
+        "u16_sparse": (1 << 30, 16, 0, "pospopcnt_u16 n=2^30 sparse Bernoulli(0.01) (2 GiB)",
+                       lambda m: synth.sparse(seed, m, 16)),
+        "u16_misaligned": ((1 << 30) + 7, 16, 2,
+                           "pospopcnt_u16 n=2^30+7 uniform bits, start 2 bytes past a 256-byte boundary",
+                           lambda m: synth.uniform_bits(seed, m, 16)),
+        "u8": (1 << 31, 8, 0, "pospopcnt_u8 n=2^31 uniform random bits (2 GiB)",
+               lambda m: synth.uniform_bits(seed, m, 8)),
+        "onehot": (1 << 31, -16, 0, "fused one-hot encode + count: 2^31 u8 ids, Zipf(1.1) over 16 categories (2 GiB)",
+                   lambda m: synth.categorical_ids(seed, m, zipf16, np.uint8)),
+        "popcount": (1 << 31, 1, 0, "array popcount of 2 GiB of uniform random bits",
+                     lambda m: synth.uniform_bytes(seed, m)),
+        "u64": (1 << 28, 64, 0, "pospopcnt_u64 n=2^28 uniform random bits (2 GiB)",
+                lambda m: synth.uniform_bits(seed, m, 64)),
+        "u32": (1 << 29, 32, 0, "pospopcnt_u32 n=2^29 uniform random bits (2 GiB)",
+                lambda m: synth.uniform_bits(seed, m, 32)),
+    }
+    if kind not in table:
+        raise ValueError(kind)
+    n, width, offset, desc, gen = table[kind]
+    return gen(min(n, limit or n)), width, offset, desc
 
 
-def cpu_baseline(words, width, budget_s=8.0):
-    """The oracle as it stands, all host cores, on a bounded sample of the
-    same input: 2^26-word chunks until budget_s of wall time has passed."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the ISA)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.machine()
+
+
+def cpu_baseline(words, width, onehot_k=0, budget_s=8.0):
+    """The oracle as it stands on a bounded sample of the same input: 2^26-word
+    chunks until budget_s of wall time has passed.  pospopcnt runs on all host
+    cores (plus a one-core figure on the first 2^25 words); the popcount and
+    one-hot oracles are single-threaded."""
     import oracle
     cores = os.cpu_count() or 1
     chunk = 1 << 26
     done, t0, used = 0, time.perf_counter(), 1
     while done < words.size:
-        _, used = oracle.pospopcnt_mt(words[done: done + chunk], width, cores)
-        done += min(chunk, words.size - done)
+        part = words[done: done + chunk]
+        if onehot_k:
+            oracle.onehot_counts(part, onehot_k)
+        elif width == 1:
+            oracle.popcount(part)
+        else:
+            _, used = oracle.pospopcnt_mt(part, width, cores)
+        done += part.size
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    nbytes = done * (width // 8)
-    return {"value": round(nbytes / dt / 1e9, 4), "unit": UNIT, "cores": used, "kind": "oracle",
-            "sample": f"first {done} of {words.size} words ({nbytes / 2**20:.0f} MiB) of the same input, "
-                      f"{dt:.1f} s wall on {used} threads"}
+    nbytes = done * words.itemsize
+    what = "one-hot encode + count" if onehot_k else "popcount" if width == 1 else "pospopcnt"
+    out = {"value": round(nbytes / dt / 1e9, 4), "unit": UNIT, "cores": used, "kind": "oracle",
+           "sample": f"{what} oracle on the first {done} of {words.size} words ({nbytes / 2**20:.0f} MiB) "
+                     f"of the same input, {dt:.1f} s wall on {used} threads",
+           "cpu_model": cpu_model(), "host_cores": cores}
+    if not onehot_k and width != 1 and used > 1:
+        part = words[: 1 << 25]
+        t1 = time.perf_counter()
+        oracle.pospopcnt_mt(part, width, 1)
+        out["single_core_value"] = round(part.size * words.itemsize / (time.perf_counter() - t1) / 1e9, 4)
+    return out
 
 
 def run_plain(args, world, rank, local):
@@ -334,7 +380,7 @@ def run_plain(args, world, rank, local):
             + f" (8-bit ids, k = {onehot_k})"
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_source": f"{peak_src} (copy bandwidth)",
-                "traffic": profiled_traffic(f"{kname}_u{width}", nbytes),
+                "traffic": profiled_traffic(f"onehot_k{onehot_k}" if onehot_k else f"{kname}_u{width}", nbytes),
                 "kernel": f"{kernel_label} (+ a {counts_bytes}-byte memset)"}
     out = None
     if rank == 0:
@@ -359,8 +405,8 @@ def run_plain(args, world, rank, local):
             "gpu_launches": int(launches),
             "clocks": clocks.summary(),
         }
-        if not args.no_cpu_baseline and world == 1 and not onehot_k:
-            out["cpu_baseline"] = cpu_baseline(words, max(width, 8))
+        if not args.no_cpu_baseline and world == 1:
+            out["cpu_baseline"] = cpu_baseline(words, width, onehot_k)
     return out
 
 
@@ -698,32 +744,51 @@ def run_e2e(args, world, rank, local):
             "frac_of_link": round(res["pinned_in_place_GBps"] / res["memcpy_pinned_GBps"], 4)}
 
 
+REFERENCE_WORKLOADS = ("u16", "u16_onehot", "u16_sparse", "u16_misaligned", "u8", "u32", "u64", "popcount", "onehot")
+
+
 def run_reference(args, world, rank):
-    """The reference arm: the scalar CPU oracle on the host cores, each step
-    a bounded 2^26-word sample of the same workload."""
+    """The reference arm: the CPU oracle on the host cores, on the same
+    workload and config as our arm, each step a bounded sample of it (its
+    first 2^26 words, which the generators make identically)."""
     if rank != 0:
         return None
     import oracle
-    import synth
-    width = {"u8": 8, "u32": 32}.get(args.workload, 16)
-    words = synth.uniform_bits(0, (1 << 27) // (width // 8), width)
+    kind = args.workload if args.workload in REFERENCE_WORKLOADS else "u16"
+    words, width, offset, desc = make_input(kind, seed=0, log2_words=args.log2_words, limit=1 << 26)
+    onehot_k = -width if width < 0 else 0
     cores = os.cpu_count() or 1
+
+    def step():
+        if onehot_k:
+            oracle.onehot_counts(words, onehot_k)
+            return 1
+        if width == 1:
+            oracle.popcount(words)
+            return 1
+        return oracle.pospopcnt_mt(words, width, cores)[1]
+
     for _ in range(args.warmup):
-        oracle.pospopcnt_mt(words, width, cores)
+        step()
     t0 = time.perf_counter()
     used = 1
     for _ in range(args.steps):
-        _, used = oracle.pospopcnt_mt(words, width, cores)
+        used = step()
     dt = time.perf_counter() - t0
-    nbytes = words.size * (width // 8)
+    nbytes = words.size * words.itemsize
     value = nbytes * args.steps / dt / 1e9
-    return {"impl": "reference", "metric": METRIC if width == 16 else f"pospopcnt_u{width} GB/s",
+    metric = METRIC if width == 16 else ("onehot_counts GB/s" if onehot_k else
+                                         "popcount GB/s" if width == 1 else f"pospopcnt_u{width} GB/s")
+    sample = f"the first {words.size} words ({nbytes >> 20} MiB) of the workload per step, {used} threads"
+    return {"impl": "reference", "metric": metric,
             "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(dt * 1e3 / args.steps, 3), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": f"u{width}", "data": "synthetic",
-            "config": {"workload": f"u{width} uniform random bits, CPU oracle sample of {nbytes >> 20} MiB per step"},
+            "vs_baseline": None, "dtype": "u8" if width in (1, -16) else f"u{width}",
+            "data": "synthetic (seeded SplitMix64 on the host)",
+            "config": {"workload": desc, "width": 1 if onehot_k else width, "start_offset_bytes": offset,
+                       "parallelism": "replicas x1", "sample_per_step": sample},
             "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": used, "kind": "oracle",
-                             "sample": f"{words.size} words ({nbytes >> 20} MiB) per step"},
+                             "sample": sample, "cpu_model": cpu_model(), "host_cores": cores},
             "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
 
