@@ -478,6 +478,10 @@ def run_batched(args, world, rank, local):
     out = torch.empty((nseg, 16), dtype=torch.int64, device=dev)
     s = torch.cuda.Stream(dev)
     s.wait_stream(torch.cuda.current_stream(dev))
+    tuned = None
+    if args.batched_autotune:  # tune the launch on this layout first (installed for width 16)
+        best, best_ms = ppc.pospopcnt_batched_autotune(x, d_off, 16, counts=out, stream=s)
+        tuned = {"config": best, "autotune_ms_per_call": round(best_ms, 4)}
     with torch.cuda.stream(s):
         for _ in range(max(args.warmup, 1)):
             ppc.pospopcnt_batched(x, d_off, 16, counts=out, stream=s)
@@ -530,7 +534,9 @@ def run_batched(args, world, rank, local):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
             "data": "synthetic", "config": {"workload": "20,000 segments log-uniform [1, 2^20] words, one-hot "
                                                         "rotated Zipf(1.1), one graph-replayed batched launch",
-                                            "total_bytes": total},
+                                            "total_bytes": total,
+                                            "launch_config": ppc.pospopcnt_batched_get_config(16),
+                                            "autotuned": tuned},
             "batched_GBps": round(total / (batched_ms * 1e-3) / 1e9, 1),
             "plain_launches": {"ms": round(plain_ms, 3), "segments_per_s": round(nseg / (plain_ms * 1e-3), 1),
                                "graph_ms": round(plain_graph_ms, 3),
@@ -804,6 +810,8 @@ def main(argv=None):
                             "sweep", "batched",
                             "kernels", "autotune", "serve", "e2e"])
     p.add_argument("--batched-nseg", type=int, default=20000)
+    p.add_argument("--batched-autotune", action="store_true",
+                   help="batched workload: autotune the launch on the layout before timing")
     p.add_argument("--serve-rate", type=float, default=50000.0)
     p.add_argument("--serve-seconds", type=float, default=60.0)
     p.add_argument("--serve-slots", type=int, default=16, help="batches in flight (continuous batching)")

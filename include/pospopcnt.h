@@ -166,6 +166,34 @@ int pospopcnt_host_is_mapped(const void* h_in, size_t nbytes);
 int pospopcnt_batched(const void* d_in, const int64_t* d_offsets, size_t nseg, int width,
                       uint64_t* d_counts, cudaStream_t stream);
 
+/* Launch parameters of the batched form, per device and width.  unit_bytes:
+ * the scheduling unit the warps claim from the work queue (4 KiB .. 1 MiB, a
+ * multiple of 128); blocks_per_sm: CTAs per SM of the persistent grid (0: as
+ * many as fit; more than fit is clamped).  Defaults: 16 KiB, 0.  The
+ * paper's method has no such parameters; they tune the launch of the
+ * segmented form (§5 notes that fixed costs dominate small inputs, which
+ * these trade against load balance). */
+typedef struct {
+  int unit_bytes;
+  int blocks_per_sm;
+} pospopcnt_batched_config;
+
+/* The configuration pospopcnt_batched (and its checked and graph forms)
+ * uses for `width` on the current device. */
+int pospopcnt_batched_get_config(int width, pospopcnt_batched_config* cfg);
+/* Installs cfg for `width` on the current device (NULL: back to the
+ * default).  POSPOPCNT_ERR_INVALID for an out-of-range field. */
+int pospopcnt_batched_set_config(int width, const pospopcnt_batched_config* cfg);
+/* Times every unit size in {4, 8, 16, 32, 64} KiB x CTAs per SM in {1, 2,
+ * as many as fit} on the caller's own layout (warm-up + 5 timed calls each,
+ * on `stream`, synchronous), checks that all of them produce identical rows
+ * (POSPOPCNT_ERR_INVALID and nothing installed if not), installs the fastest
+ * for `width` on the current device and returns it (and its mean time per
+ * call in ms if best_ms is not NULL).  d_counts receives the rows. */
+int pospopcnt_batched_autotune(const void* d_in, const int64_t* d_offsets, size_t nseg, int width,
+                               uint64_t* d_counts, pospopcnt_batched_config* best, float* best_ms,
+                               cudaStream_t stream);
+
 /* A pospopcnt_batched call (its memset and its kernel) captured once into
  * an instantiated CUDA graph; each pospopcnt_graph_launch recounts the same
  * buffers (their contents may change between launches) with a single graph

@@ -58,6 +58,14 @@ class Config(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class BatchedConfig(ctypes.Structure):
+    """pospopcnt_batched_config: unit_bytes, blocks_per_sm."""
+    _fields_ = [("unit_bytes", ctypes.c_int), ("blocks_per_sm", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class ServerConfig(ctypes.Structure):
     """pospopcnt_server_config."""
     _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_int),
@@ -125,6 +133,9 @@ def _declare(lib):
         "pospopcnt_batched_noalloc": (i32, [vp, vp, sz, i32, vp, vp]),
         "pospopcnt_batched_checked": (i32, [vp, sz, vp, sz, i32, vp, vp]),
         "pospopcnt_batched_graph_create": (i32, [vp, vp, sz, i32, vp, P(vp)]),
+        "pospopcnt_batched_get_config": (i32, [i32, P(BatchedConfig)]),
+        "pospopcnt_batched_set_config": (i32, [i32, P(BatchedConfig)]),
+        "pospopcnt_batched_autotune": (i32, [vp, vp, sz, i32, vp, P(BatchedConfig), P(ctypes.c_float), vp]),
         "pospopcnt_graph_launch": (i32, [vp, vp]),
         "pospopcnt_graph_destroy": (i32, [vp]),
         "pospopcnt_check_device_error": (i32, [vp]),
@@ -338,6 +349,43 @@ def pospopcnt_batched(x, offsets, width: int, counts=None, stream=None):
         _check(_lib().pospopcnt_batched(ptr, offsets.data_ptr(), nseg, width, out.data_ptr(),
                                         _stream_handle(stream, x.device)), "pospopcnt_batched")
     return out
+
+
+def pospopcnt_batched_get_config(width: int, device=None) -> dict:
+    """The batched form's launch configuration for `width` (dict)."""
+    torch = _torch()
+    c = BatchedConfig()
+    with torch.cuda.device(device if device is not None else torch.cuda.current_device()):
+        _check(_lib().pospopcnt_batched_get_config(width, ctypes.byref(c)), "pospopcnt_batched_get_config")
+    return c.as_dict()
+
+
+def pospopcnt_batched_set_config(width: int, cfg, device=None) -> None:
+    """Installs cfg (dict with unit_bytes, blocks_per_sm; None: the default)."""
+    torch = _torch()
+    ref = None
+    if cfg is not None:
+        c = BatchedConfig(int(cfg["unit_bytes"]), int(cfg.get("blocks_per_sm", 0)))
+        ref = ctypes.byref(c)
+    with torch.cuda.device(device if device is not None else torch.cuda.current_device()):
+        _check(_lib().pospopcnt_batched_set_config(width, ref), "pospopcnt_batched_set_config")
+
+
+def pospopcnt_batched_autotune(x, offsets, width: int, counts=None, stream=None):
+    """Times the batched form's launch configurations on this layout; installs
+    and returns the fastest (dict) and its time per call in ms."""
+    torch = _torch()
+    ptr, _ = _words(x, width)
+    if offsets.dtype != torch.int64 or not offsets.is_cuda or not offsets.is_contiguous():
+        raise ValueError("offsets must be a contiguous CUDA int64 tensor")
+    nseg = max(offsets.numel() - 1, 0)
+    out = _counts_out(counts, width, nseg, x.device)
+    c, ms = BatchedConfig(), ctypes.c_float()
+    with torch.cuda.device(x.device):
+        _check(_lib().pospopcnt_batched_autotune(ptr, offsets.data_ptr(), nseg, width, out.data_ptr(),
+                                                 ctypes.byref(c), ctypes.byref(ms), _stream_handle(stream, x.device)),
+               "pospopcnt_batched_autotune")
+    return c.as_dict(), ms.value
 
 
 def pospopcnt_batched_graph_create(x, offsets, width: int, counts) -> int:

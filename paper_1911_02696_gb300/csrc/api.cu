@@ -25,6 +25,11 @@ DeviceState g_state[MAX_DEVICES];
 std::unordered_map<cudaStream_t, int> g_slots[MAX_DEVICES];
 pospopcnt_config g_cfg[MAX_DEVICES][4][NCLASSES];
 bool g_cfg_ready[MAX_DEVICES] = {};
+// Batched form, per device and width (8, 16, 32): 16 KiB units, as many
+// CTAs per SM as fit, until pospopcnt_batched_set_config/autotune.
+pospopcnt_batched_config g_bcfg[MAX_DEVICES][3] = {};
+bool g_bcfg_set[MAX_DEVICES][3] = {};
+constexpr pospopcnt_batched_config BATCHED_DEFAULT = {16384, 0};
 std::mutex g_host_mutex[MAX_DEVICES];
 std::atomic<uint64_t> g_launches{0};
 thread_local int t_last_cuda = 0;
@@ -423,26 +428,39 @@ int pospopcnt_host_is_mapped(const void* h_in, size_t nbytes) {
 namespace ppc {
 namespace {
 int batched_impl(const void* d_in, const int64_t* d_offsets, size_t nseg, int width, uint64_t* d_counts,
-                 cudaStream_t stream, bool checked, uint64_t n_words);
+                 cudaStream_t stream, bool checked, uint64_t n_words, const pospopcnt_batched_config* cfg);
+bool batched_config_valid(const pospopcnt_batched_config& c);
+pospopcnt_batched_config batched_config(int device, int width);
 }  // namespace
 }  // namespace ppc
 
 int pospopcnt_batched(const void* d_in, const int64_t* d_offsets, size_t nseg, int width, uint64_t* d_counts,
                       cudaStream_t stream) {
-  return ppc::batched_impl(d_in, d_offsets, nseg, width, d_counts, stream, false, 0);
+  return ppc::batched_impl(d_in, d_offsets, nseg, width, d_counts, stream, false, 0, nullptr);
 }
 
 int pospopcnt_batched_checked(const void* d_in, size_t n_words, const int64_t* d_offsets, size_t nseg, int width,
                               uint64_t* d_counts, cudaStream_t stream) {
-  return ppc::batched_impl(d_in, d_offsets, nseg, width, d_counts, stream, true, n_words);
+  return ppc::batched_impl(d_in, d_offsets, nseg, width, d_counts, stream, true, n_words, nullptr);
 }
 
 }  // extern "C"
 
 namespace ppc {
 namespace {
+pospopcnt_batched_config batched_config(int device, int width) {
+  std::lock_guard<std::mutex> lk(g_mutex);
+  const int w = width_index(width);
+  return g_bcfg_set[device][w] ? g_bcfg[device][w] : BATCHED_DEFAULT;
+}
+
+bool batched_config_valid(const pospopcnt_batched_config& c) {
+  return c.unit_bytes >= 4096 && c.unit_bytes <= (1 << 20) && c.unit_bytes % 128 == 0 && c.blocks_per_sm >= 0 &&
+         c.blocks_per_sm <= 32;
+}
+
 int batched_impl(const void* d_in, const int64_t* d_offsets, size_t nseg, int width, uint64_t* d_counts,
-                 cudaStream_t stream, bool checked, uint64_t n_words) {
+                 cudaStream_t stream, bool checked, uint64_t n_words, const pospopcnt_batched_config* cfg) {
   if (width != 8 && width != 16 && width != 32) return POSPOPCNT_ERR_INVALID;
   if (nseg == 0) return POSPOPCNT_OK;
   if (!d_in || !d_offsets || !d_counts) return POSPOPCNT_ERR_INVALID;
@@ -470,9 +488,9 @@ int batched_impl(const void* d_in, const int64_t* d_offsets, size_t nseg, int wi
   if (e != cudaSuccess) return cuda_fail(e);
   void* q = static_cast<char*>(st->d_queue) + size_t(slot) * QUEUE_SLOT_BYTES;
   if (checked && (rc = launch_offsets_check(*st, d_offsets, nseg, n_words, q, stream)) != POSPOPCNT_OK) return rc;
-  const int tile_words = (16 * 1024) / (width / 8);  // 16 KiB scheduling unit
+  const pospopcnt_batched_config c = cfg ? *cfg : batched_config(st->device, width);
   return launch_batched(*st, d_in, d_offsets, nseg, width, reinterpret_cast<unsigned long long*>(d_counts), q,
-                        tile_words, stream);
+                        c.unit_bytes / (width / 8), c.blocks_per_sm, stream);
 }
 }  // namespace
 }  // namespace ppc
@@ -659,6 +677,87 @@ int pospopcnt_autotune(int width, const void* d_in, size_t n, uint64_t* d_scratc
   if (best_ms) *best_ms = best_t;
   std::lock_guard<std::mutex> lk(g_mutex);
   g_cfg[st->device][width_index(width)][size_class(uint64_t(n) * uint64_t(width / 8))] = *best;
+  return POSPOPCNT_OK;
+}
+
+int pospopcnt_batched_get_config(int width, pospopcnt_batched_config* cfg) {
+  if ((width != 8 && width != 16 && width != 32) || !cfg) return POSPOPCNT_ERR_INVALID;
+  int rc = POSPOPCNT_OK;
+  DeviceState* st = current_state(&rc);
+  if (!st) return rc;
+  *cfg = batched_config(st->device, width);
+  return POSPOPCNT_OK;
+}
+
+int pospopcnt_batched_set_config(int width, const pospopcnt_batched_config* cfg) {
+  if ((width != 8 && width != 16 && width != 32) || (cfg && !batched_config_valid(*cfg))) return POSPOPCNT_ERR_INVALID;
+  int rc = POSPOPCNT_OK;
+  DeviceState* st = current_state(&rc);
+  if (!st) return rc;
+  std::lock_guard<std::mutex> lk(g_mutex);
+  const int w = width_index(width);
+  g_bcfg_set[st->device][w] = cfg != nullptr;
+  if (cfg) g_bcfg[st->device][w] = *cfg;
+  return POSPOPCNT_OK;
+}
+
+int pospopcnt_batched_autotune(const void* d_in, const int64_t* d_offsets, size_t nseg, int width,
+                               uint64_t* d_counts, pospopcnt_batched_config* best, float* best_ms,
+                               cudaStream_t stream) {
+  if (!best || nseg == 0) return POSPOPCNT_ERR_INVALID;
+  int rc = POSPOPCNT_OK;
+  DeviceState* st = current_state(&rc);
+  if (!st) return rc;
+  std::vector<pospopcnt_batched_config> cands;
+  for (int unit : {4096, 8192, 16384, 32768, 65536})
+    for (int bps : {1, 2, 0}) cands.push_back(pospopcnt_batched_config{unit, bps});
+  const size_t row_words = size_t(width) * nseg;
+  std::vector<uint64_t> ref(row_words), got(row_words);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess) return cuda_fail(e);
+  if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(e);
+  }
+  float best_t = 1e30f;
+  int best_i = -1;
+  const int reps = 5;
+  for (size_t i = 0; i < cands.size() && rc == POSPOPCNT_OK; ++i) {
+    rc = batched_impl(d_in, d_offsets, nseg, width, d_counts, stream, false, 0, &cands[i]);  // warm-up
+    if (rc != POSPOPCNT_OK) break;
+    cudaEventRecord(e0, stream);
+    for (int r = 0; r < reps && rc == POSPOPCNT_OK; ++r)
+      rc = batched_impl(d_in, d_offsets, nseg, width, d_counts, stream, false, 0, &cands[i]);
+    cudaEventRecord(e1, stream);
+    if (rc != POSPOPCNT_OK) break;
+    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
+      rc = cuda_fail(e);
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= reps;
+    if ((e = cudaMemcpy(got.data(), d_counts, sizeof(uint64_t) * row_words, cudaMemcpyDeviceToHost)) != cudaSuccess) {
+      rc = cuda_fail(e);
+      break;
+    }
+    if (i == 0) {
+      ref = got;
+    } else if (got != ref) {
+      rc = POSPOPCNT_ERR_INVALID;  // candidates disagree: refuse to tune
+      break;
+    }
+    if (ms < best_t) best_t = ms, best_i = int(i);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != POSPOPCNT_OK) return rc;
+  *best = cands[size_t(best_i)];
+  if (best_ms) *best_ms = best_t;
+  std::lock_guard<std::mutex> lk(g_mutex);
+  g_bcfg[st->device][width_index(width)] = *best;
+  g_bcfg_set[st->device][width_index(width)] = true;
   return POSPOPCNT_OK;
 }
 

@@ -225,13 +225,15 @@ __global__ void __launch_bounds__(BT_THREADS, bt_batched_min_blocks<K>::value) b
 }
 
 template <int K>
-static int launch_batched_k(const DeviceState& st, const BatchedArgs& a, cudaStream_t stream) {
+static int launch_batched_k(const DeviceState& st, const BatchedArgs& a, cudaStream_t stream,
+                            int blocks_per_sm = 0) {
   auto kern = batched_kernel<K>;
   if (const cudaError_t e = ensure_dynamic_smem<batched_kernel<K>>(st.device, int(BT_RING_SMEM))) return cuda_fail(e);
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, BT_THREADS, BT_RING_SMEM) != cudaSuccess || occ < 1)
     occ = 1;
-  const unsigned grid = unsigned(st.sms) * unsigned(occ);
+  const int bps = blocks_per_sm > 0 && blocks_per_sm < occ ? blocks_per_sm : occ;
+  const unsigned grid = unsigned(st.sms) * unsigned(bps);
   kern<<<grid, BT_THREADS, BT_RING_SMEM, stream>>>(a);
   note_launch();
   const cudaError_t e = cudaGetLastError();
@@ -269,7 +271,7 @@ int launch_offsets_check(const DeviceState& st, const int64_t* d_offsets, size_t
 
 int launch_batched(const DeviceState& st, const void* d_in, const int64_t* d_offsets, size_t nseg,
                    int width, unsigned long long* d_counts, void* queue_slot, int tile_words,
-                   cudaStream_t stream) {
+                   int blocks_per_sm, cudaStream_t stream) {
   BatchedArgs a;
   a.base = static_cast<const uint8_t*>(d_in);
   a.offsets = d_offsets;
@@ -279,9 +281,9 @@ int launch_batched(const DeviceState& st, const void* d_in, const int64_t* d_off
   a.tile_words = uint64_t(tile_words);
   a.err = st.d_err;
   switch (width) {
-    case 8: return launch_batched_k<8>(st, a, stream);
-    case 16: return launch_batched_k<16>(st, a, stream);
-    case 32: return launch_batched_k<32>(st, a, stream);
+    case 8: return launch_batched_k<8>(st, a, stream, blocks_per_sm);
+    case 16: return launch_batched_k<16>(st, a, stream, blocks_per_sm);
+    case 32: return launch_batched_k<32>(st, a, stream, blocks_per_sm);
   }
   return POSPOPCNT_ERR_INVALID;
 }

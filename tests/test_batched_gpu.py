@@ -190,3 +190,34 @@ def test_native_graph_api():
             assert np.array_equal(out.cpu().numpy().view(np.uint64), oracle.pospopcnt_segments(words, off, 16))
     finally:
         ppc.pospopcnt_graph_destroy(g)
+
+
+def test_batched_autotune_and_config():
+    """The autotuner times every unit size x CTAs-per-SM on the caller's
+    layout, refuses to install unless all agree, and installs the fastest;
+    counts stay bit-exact under every configuration, and out-of-range
+    configurations are rejected."""
+    rng = np.random.default_rng(10)
+    off = _layout(rng, 1500, 40000, start=5)
+    words = synth.uniform_bits(10, int(off[-1]) + 3, 16)
+    _, x = _dev(words, 2)
+    d_off = torch.from_numpy(off).cuda()
+    ref = oracle.pospopcnt_segments(words, off, 16)
+    try:
+        best, ms = ppc.pospopcnt_batched_autotune(x, d_off, 16)
+        assert ms > 0 and best["unit_bytes"] in (4096, 8192, 16384, 32768, 65536)
+        assert ppc.pospopcnt_batched_get_config(16) == best
+        got = ppc.pospopcnt_batched(x, d_off, 16)
+        assert np.array_equal(got.cpu().numpy().view(np.uint64), ref)
+        for cfg in ({"unit_bytes": 4096, "blocks_per_sm": 1}, {"unit_bytes": 1 << 20, "blocks_per_sm": 32},
+                    {"unit_bytes": 8192 + 128, "blocks_per_sm": 0}):
+            ppc.pospopcnt_batched_set_config(16, cfg)
+            got = ppc.pospopcnt_batched(x, d_off, 16)
+            assert np.array_equal(got.cpu().numpy().view(np.uint64), ref), cfg
+        for bad in ({"unit_bytes": 2048}, {"unit_bytes": 4096 + 64}, {"unit_bytes": 2 << 20},
+                    {"unit_bytes": 4096, "blocks_per_sm": -1}, {"unit_bytes": 4096, "blocks_per_sm": 33}):
+            with pytest.raises(ppc.PospopcntError):
+                ppc.pospopcnt_batched_set_config(16, bad)
+    finally:
+        ppc.pospopcnt_batched_set_config(16, None)
+    assert ppc.pospopcnt_batched_get_config(16) == {"unit_bytes": 16384, "blocks_per_sm": 0}
