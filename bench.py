@@ -389,7 +389,9 @@ def run_plain(args, world, rank, local):
                                                   "popcount GB/s" if width == 1 else f"pospopcnt_u{width} GB/s"),
             "value": round(value, 2),
             "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(max_ms / args.steps, 5), "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": round(max_ms / args.steps, 5),
+            "ms_per_step_median": round(statistics.median(per_step), 5), "ms_per_step_min": round(min(per_step), 5),
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u8" if width == 1 else f"u{width}",
             "data": "synthetic (seeded SplitMix64 on the host)",
             "config": {"workload": desc, "n_words": int(words.size), "width": width, "start_offset_bytes": offset,
@@ -542,6 +544,57 @@ def run_batched(args, world, rank, local):
                                "graph_ms": round(plain_graph_ms, 3),
                                "graph_segments_per_s": round(nseg / (plain_graph_ms * 1e-3), 1)},
             "speedup_vs_plain": round(plain_ms / batched_ms, 2)}
+
+
+def run_peaks(args, world, rank, local):
+    """Measured rooflines beside the driver's copy figure: a read-only scan
+    (torch's fp32 sum over 2 GiB: every byte read once, nothing written),
+    a device-to-device copy (read + write bytes), and the u16 pospopcnt
+    kernel on the same buffer; CUDA events, best and median of the reps,
+    inputs larger than L2."""
+    import torch
+    import paper_1911_02696_gb300 as ppc
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ppc.pospopcnt_init(local)
+    nbytes = 2 << 30
+    a = torch.randint(0, 1 << 30, (nbytes // 4,), dtype=torch.int32, device=dev)
+    b = torch.empty_like(a)
+    counts = torch.empty(16, dtype=torch.int64, device=dev)
+    x16 = a.view(torch.uint8)
+    reps = max(10, min(args.steps, 50))
+
+    def timed(fn):  # back to back on the current stream, one event between reps
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
+        torch.cuda.synchronize()
+        ev[0].record()
+        for i in range(reps):
+            fn()
+            ev[i + 1].record()
+        torch.cuda.synchronize()
+        ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(reps)]
+        return min(ms), statistics.median(ms)
+
+    af = a.view(torch.float32)
+    res = {}
+    for name, fn, moved in (("read_sum_fp32", lambda: torch.sum(af), nbytes),
+                            ("copy_d2d", lambda: b.copy_(a), 2 * nbytes),
+                            ("pospopcnt_u16", lambda: ppc.pospopcnt_u16(x16, counts=counts), nbytes)):
+        best, med = timed(fn)
+        res[name] = {"bytes_moved": moved, "best_ms": round(best, 4), "median_ms": round(med, 4),
+                     "best_GBps": round(moved / (best * 1e-3) / 1e9, 1),
+                     "median_GBps": round(moved / (med * 1e-3) / 1e9, 1)}
+    peak, src = peak_hbm()
+    if rank != 0:
+        return None
+    return {"metric": "measured rooflines GB/s", "value": res["read_sum_fp32"]["best_GBps"], "unit": UNIT,
+            "n_gpus": world, "steps": reps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic (torch.randint on the device)",
+            "config": {"workload": "2 GiB: read-only fp32 sum, device-to-device copy, pospopcnt_u16"},
+            "results": res, "copy_peak_file": {"hbm_gbs": peak, "source": src},
+            "nominal_hbm_GBps": 7900.0}
 
 
 def candidate_configs():
@@ -808,7 +861,7 @@ def main(argv=None):
     p.add_argument("--workload", default="u16",
                    choices=["u16", "u16_onehot", "u16_sparse", "u16_misaligned", "u8", "u32", "u64", "popcount", "onehot",
                             "sweep", "batched",
-                            "kernels", "autotune", "serve", "e2e"])
+                            "kernels", "autotune", "serve", "e2e", "peaks"])
     p.add_argument("--batched-nseg", type=int, default=20000)
     p.add_argument("--batched-autotune", action="store_true",
                    help="batched workload: autotune the launch on the layout before timing")
@@ -850,6 +903,8 @@ def main(argv=None):
             out = run_serve(args, world, rank, local)
         elif args.workload == "e2e":
             out = run_e2e(args, world, rank, local)
+        elif args.workload == "peaks":
+            out = run_peaks(args, world, rank, local)
         else:
             out = run_plain(args, world, rank, local)
         if world > 1:
