@@ -715,20 +715,37 @@ def run_serve(args, world, rank, local):
             ppc.pospopcnt_server_run_trace(srv, tr["t_arrival"][:k] - tr["t_arrival"][0], tr["width"][:k],
                                            addr[:k], tr["nwords"][:k])
             t0 = time.perf_counter()
-            lat, counts, status = ppc.pospopcnt_server_run_trace(srv, tr["t_arrival"], tr["width"], addr,
-                                                                 tr["nwords"], want_counts=True)
+            lat, counts, status, stages = ppc.pospopcnt_server_run_trace(srv, tr["t_arrival"], tr["width"], addr,
+                                                                         tr["nwords"], want_counts=True,
+                                                                         want_stages=True)
             wall = time.perf_counter() - t0
             st = ppc.pospopcnt_server_get_stats(srv)
         finally:
             ppc.pospopcnt_server_destroy(srv)
         assert np.all(status == 0), "requests failed"
         q = np.percentile(lat, [50, 99, 99.9]) * 1e3
+        large = nbytes >= int(args.serve_large_mib * (1 << 20))
+
+        def breakdown(mask):  # microseconds from arrival: p50 / p99 of each stage boundary
+            if not mask.any():
+                return None
+            st_us = stages[mask] * 1e6
+            names = ("admit", "launch", "done")
+            out = {"requests": int(mask.sum())}
+            for k, nm in enumerate(names):
+                out[f"{nm}_p50_us"] = round(float(np.percentile(st_us[:, k], 50)), 2)
+                out[f"{nm}_p99_us"] = round(float(np.percentile(st_us[:, k], 99)), 2)
+            gpu = st_us[:, 2] - st_us[:, 1]
+            out["launch_to_done_p50_us"] = round(float(np.percentile(gpu, 50)), 2)
+            out["launch_to_done_p99_us"] = round(float(np.percentile(gpu, 99)), 2)
+            return out
         return {"p50_ms": round(float(q[0]), 4), "p99_ms": round(float(q[1]), 4), "p999_ms": round(float(q[2]), 4),
                 "max_ms": round(float(lat.max()) * 1e3, 4), "mean_ms": round(float(lat.mean()) * 1e3, 4),
                 "aggregate_GBps": round(total / wall / 1e9, 2), "wall_s": round(wall, 3),
                 "batches": st["batches"], "mean_jobs_per_batch": round(st["jobs_in_batches"] / max(st["batches"], 1), 2),
                 "max_batch": st["max_batch"], "deferrals": st["deferrals"],
-                "max_GiB_in_flight": round(st["max_bytes_in_flight"] / 2**30, 3)}, counts
+                "max_GiB_in_flight": round(st["max_bytes_in_flight"] / 2**30, 3),
+                "stages_small": breakdown(~large), "stages_large": breakdown(large)}, counts
 
     batched, c_b = serve(False)
     plain, c_p = serve(True)

@@ -312,6 +312,15 @@ int pospopcnt_server_run_trace(pospopcnt_server* server, size_t n, const double*
                                const uint64_t* d_addr, const uint64_t* nwords, double* latency_out,
                                uint64_t* counts_out, int* status_out);
 
+/* pospopcnt_server_run_trace that also records where each request's time
+ * went: stages_out (optional, n x 3 doubles) receives, per request, the
+ * seconds from its scheduled arrival to its admission (payload within the
+ * HBM budget), to the launch that carries it, and to its completion seen on
+ * the host.  Entries of requests that did not complete stay NaN. */
+int pospopcnt_server_run_trace_timed(pospopcnt_server* server, size_t n, const double* t_arrival, const int* width,
+                                     const uint64_t* d_addr, const uint64_t* nwords, double* latency_out,
+                                     uint64_t* counts_out, int* status_out, double* stages_out);
+
 int pospopcnt_server_get_stats(pospopcnt_server* server, pospopcnt_server_stats* out);
 
 /* The server's admission policy on a mock clock (host only, no device): jobs

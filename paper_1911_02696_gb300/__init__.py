@@ -29,7 +29,8 @@ __all__ = [
     "pospopcnt_get_config", "pospopcnt_set_config", "pospopcnt_autotune", "pospopcnt_strerror",
     "pospopcnt_last_cuda_error", "pospopcnt_launch_count", "pospopcnt_selftest_timeout", "KERNELS",
     "Config", "pospopcnt_server_create", "pospopcnt_server_destroy", "pospopcnt_server_submit",
-    "pospopcnt_server_poll", "pospopcnt_server_run_trace", "pospopcnt_server_get_stats",
+    "pospopcnt_server_poll", "pospopcnt_server_run_trace", "pospopcnt_server_run_trace_timed",
+    "pospopcnt_server_get_stats",
     "pospopcnt_admission_simulate",
 ]
 
@@ -152,6 +153,7 @@ def _declare(lib):
         "pospopcnt_server_submit": (i32, [vp, i32, vp, sz, u64]),
         "pospopcnt_server_poll": (i32, [vp, P(Result), i32, P(i32)]),
         "pospopcnt_server_run_trace": (i32, [vp, sz, vp, vp, vp, vp, vp, vp, vp]),
+        "pospopcnt_server_run_trace_timed": (i32, [vp, sz, vp, vp, vp, vp, vp, vp, vp, vp]),
         "pospopcnt_server_get_stats": (i32, [vp, P(ServerStats)]),
         "pospopcnt_admission_simulate": (i32, [u64, sz, vp, vp, vp, vp, vp]),
     }
@@ -561,8 +563,11 @@ def pospopcnt_server_poll(server: int, max_results: int = 1024):
     return out
 
 
-def pospopcnt_server_run_trace(server: int, t_arrival, width, d_addr, nwords, want_counts: bool = False):
-    """Replays an open-loop trace; returns (latency_s, counts or None, status)."""
+def pospopcnt_server_run_trace(server: int, t_arrival, width, d_addr, nwords, want_counts: bool = False,
+                               want_stages: bool = False):
+    """Replays an open-loop trace; returns (latency_s, counts or None, status),
+    plus, with want_stages, an n x 3 array of seconds from each request's
+    arrival to its admission, its launch and its completion."""
     t = np.ascontiguousarray(t_arrival, dtype=np.float64)
     w = np.ascontiguousarray(width, dtype=np.int32)
     a = np.ascontiguousarray(d_addr, dtype=np.uint64)
@@ -572,10 +577,12 @@ def pospopcnt_server_run_trace(server: int, t_arrival, width, d_addr, nwords, wa
     lat = np.empty(n, dtype=np.float64)
     status = np.empty(n, dtype=np.int32)
     counts = np.zeros((n, 32), dtype=np.uint64) if want_counts else None
-    _check(_lib().pospopcnt_server_run_trace(
+    stages = np.empty((n, 3), dtype=np.float64) if want_stages else None
+    _check(_lib().pospopcnt_server_run_trace_timed(
         ctypes.c_void_p(server), n, t.ctypes.data, w.ctypes.data, a.ctypes.data, nw.ctypes.data, lat.ctypes.data,
-        counts.ctypes.data if counts is not None else None, status.ctypes.data), "pospopcnt_server_run_trace")
-    return lat, counts, status
+        counts.ctypes.data if counts is not None else None, status.ctypes.data,
+        stages.ctypes.data if stages is not None else None), "pospopcnt_server_run_trace")
+    return (lat, counts, status, stages) if want_stages else (lat, counts, status)
 
 
 def pospopcnt_server_get_stats(server: int) -> dict:

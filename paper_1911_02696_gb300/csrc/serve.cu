@@ -31,9 +31,12 @@
 // Jobs of at least large_job_bytes (default 4 MiB) gain nothing from
 // batching -- their transfer time dwarfs a launch -- and would make every
 // warp of a batch add into one row; each is launched on its own slot with
-// the tuned plain count (block-level reduction), followed by a copy of its
-// counts and an event.  In per-request mode every job takes that route (the
-// comparison the batched form is measured against).
+// the tuned plain count (block-level reduction) adding into a row kept at
+// zero, followed by a one-warp kernel that publishes the counts and the flag
+// the same way.  In per-request mode every job takes that route (the
+// comparison the batched form is measured against).  Launches carry the job
+// table sized to their batch (8 or 240 entries); no event is recorded --
+// the watchdog asks the slot's stream whether it ran dry.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -71,9 +74,14 @@ struct AdmissionPolicy {
 constexpr int SERVE_MAX_JOBS = 240;  // job table in the kernel parameters (< 4 KiB)
 constexpr uint64_t SERVE_TILE_BYTES = 64 * 1024;  // one CTA: 8 warps x 8 KiB
 
+// Job table in the kernel parameters, CAP jobs at most: a launch carries
+// only the table size its batch needs (parameters are copied at every launch).
+constexpr int SERVE_SMALL_CAP = 8;
+
+template <int CAP>
 struct ServeArgs {
-  int64_t bounds[SERVE_MAX_JOBS + 1];  // virtual word offsets: job s is [bounds[s], bounds[s+1])
-  uint64_t addr[SERVE_MAX_JOBS];       // byte address of each job's first word
+  int64_t bounds[CAP + 1];  // virtual word offsets: job s is [bounds[s], bounds[s+1])
+  uint64_t addr[CAP];       // byte address of each job's first word
   uint32_t nseg;
   uint32_t ticket;                     // stored into a job's flag when its counts are final
   uint64_t tile_words;                 // multiple of 8 warps x 16 bytes
@@ -83,8 +91,9 @@ struct ServeArgs {
   unsigned* h_flags;                   // device view of pinned host memory, SERVE_MAX_JOBS
 };
 
-template <int K>
-__global__ void __launch_bounds__(BT_THREADS, bt_min_blocks<K>::value) serve_kernel(const __grid_constant__ ServeArgs a) {
+template <int K, int CAP>
+__global__ void __launch_bounds__(BT_THREADS, bt_min_blocks<K>::value)
+    serve_kernel(const __grid_constant__ ServeArgs<CAP> a) {
   constexpr int WB = K / 8;
   constexpr int SH = 5 - ilog2<K>::value;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -120,17 +129,14 @@ __global__ void __launch_bounds__(BT_THREADS, bt_min_blocks<K>::value) serve_ker
         last = __shfl_sync(FULL_MASK, last, 0);
         if (last) {
           __threadfence();
-          const unsigned long long c = lane < K ? atomicExch(row + lane, 0ull) : 0ull;
-#pragma unroll
-          for (int p = 0; p < K; ++p) {
-            const unsigned long long cp = __shfl_sync(FULL_MASK, c, p);
-            if (lane == 0) a.h_counts[s * 32 + p] = cp;
-          }
-          if (lane == 0) {
-            a.pieces[s] = 0;
-            __threadfence_system();
-            *reinterpret_cast<volatile unsigned*>(a.h_flags + s) = a.ticket;
-          }
+          // lane p moves count p to the host in one coalesced store; every
+          // storing lane fences its own store before the warp syncs and
+          // lane 0 raises the flag
+          if (lane < K) a.h_counts[s * 32 + lane] = atomicExch(row + lane, 0ull);
+          if (lane == 0) a.pieces[s] = 0;
+          __threadfence_system();
+          __syncwarp();
+          if (lane == 0) *reinterpret_cast<volatile unsigned*>(a.h_flags + s) = a.ticket;
         }
       }
       if (seg_hi >= w1 || s + 1 >= a.nseg) break;
@@ -138,6 +144,22 @@ __global__ void __launch_bounds__(BT_THREADS, bt_min_blocks<K>::value) serve_ker
       seg_lo = seg_hi;
     }
   }
+}
+
+// A job counted by a plain launch: its counts were accumulated into d_row
+// (kept zero between jobs); one warp moves them to the host, re-zeroes the
+// row and raises the job's flag, as the serving kernel does for its jobs.
+template <int K>
+__global__ void serve_publish_kernel(unsigned long long* d_row, unsigned long long* h_counts, unsigned* h_flag,
+                                     unsigned ticket) {
+  const int lane = threadIdx.x & 31;
+  if (lane < K) {
+    h_counts[lane] = d_row[lane];
+    d_row[lane] = 0;
+  }
+  __threadfence_system();
+  __syncwarp();
+  if (lane == 0) *reinterpret_cast<volatile unsigned*>(h_flag) = ticket;
 }
 
 namespace {
@@ -156,11 +178,9 @@ int widx(int w) { return w == 8 ? 0 : w == 16 ? 1 : 2; }
 
 struct Slot {
   cudaStream_t stream = nullptr;
-  cudaEvent_t done = nullptr;               // after the kernel (watchdog; per-request completion)
   unsigned long long* d_rows = nullptr;     // device SERVE_MAX_JOBS x 32, zero between batches
   unsigned* d_pieces = nullptr;             // device SERVE_MAX_JOBS
-  unsigned long long* d_single = nullptr;   // device, 32: a single job's counts (rows stay zero)
-  unsigned long long* h_single = nullptr;   // pinned: its copy on the host
+  unsigned long long* d_single = nullptr;   // device, 32: a single job's counts, zero between jobs
   unsigned long long* h_counts = nullptr;   // pinned, mapped: SERVE_MAX_JOBS x 32
   unsigned* h_flags = nullptr;              // pinned, mapped: SERVE_MAX_JOBS
   unsigned long long* dv_counts = nullptr;  // device views of h_counts / h_flags
@@ -172,7 +192,7 @@ struct Slot {
   double t_launch = 0;
   int width = 16;
   bool busy = false;
-  bool single = false;  // one job counted by a plain launch; completion by event
+  bool single = false;  // one job counted by a plain launch, published by serve_publish_kernel
 };
 
 }  // namespace
@@ -204,6 +224,7 @@ struct Server {
   std::mutex done_mu;
   std::deque<pospopcnt_result> done;
   std::atomic<double*> trace_latency{nullptr};
+  std::atomic<double*> trace_stages{nullptr};  // n x 3: admit, launch, done - arrival
   std::atomic<uint64_t*> trace_counts{nullptr};
   std::atomic<int*> trace_status{nullptr};
   std::atomic<uint64_t> total_submitted{0};
@@ -219,19 +240,24 @@ struct Server {
     double* lat = trace_latency.load(std::memory_order_acquire);
     if (lat) {
       lat[j.tag] = j.t_done - j.t_arrival;
+      if (double* stg = trace_stages.load(std::memory_order_relaxed)) {
+        stg[3 * j.tag + 0] = j.t_admit - j.t_arrival;
+        stg[3 * j.tag + 1] = j.t_launch - j.t_arrival;
+        stg[3 * j.tag + 2] = j.t_done - j.t_arrival;
+      }
       int* st_out = trace_status.load(std::memory_order_relaxed);
       uint64_t* cnt = trace_counts.load(std::memory_order_relaxed);
       if (st_out) st_out[j.tag] = status;
       if (cnt) {
         uint64_t* dst = cnt + j.tag * 32;
         std::memset(dst, 0, 32 * sizeof(uint64_t));
-        if (status == POSPOPCNT_OK) std::memcpy(dst, counts, sizeof(uint64_t) * size_t(j.width));
+        if (status == POSPOPCNT_OK && counts) std::memcpy(dst, counts, sizeof(uint64_t) * size_t(j.width));
       }
     } else {
       pospopcnt_result r{};
       r.tag = j.tag, r.status = status, r.width = j.width, r.n = j.n;
       r.t_arrival = j.t_arrival, r.t_admit = j.t_admit, r.t_launch = j.t_launch, r.t_done = j.t_done;
-      if (status == POSPOPCNT_OK) std::memcpy(r.counts, counts, sizeof(uint64_t) * size_t(j.width));
+      if (status == POSPOPCNT_OK && counts) std::memcpy(r.counts, counts, sizeof(uint64_t) * size_t(j.width));
       std::lock_guard<std::mutex> lk(done_mu);
       done.push_back(r);
     }
@@ -255,30 +281,26 @@ struct Server {
     bool any = false;
     for (Slot& s : slots) {
       if (!s.busy) continue;
-      if (s.single) {
-        const cudaError_t q = cudaEventQuery(s.done);
-        if (q == cudaErrorNotReady) continue;
-        finish(s, 0, s.h_single, q == cudaSuccess ? POSPOPCNT_OK : cuda_fail(q), now_seconds());
-      } else {
-        for (size_t i = 0; i < s.jobs.size(); ++i) {
-          if (s.finished[i]) continue;
-          if (__atomic_load_n(s.h_flags + i, __ATOMIC_ACQUIRE) != s.ticket) continue;
-          finish(s, i, s.h_counts + i * 32, POSPOPCNT_OK, now_seconds());
-          any = true;
-        }
-        // watchdog: the kernel ended (or failed) without publishing every job
-        if (s.remaining && now_seconds() - s.t_launch > 0.5) {
-          const cudaError_t q = cudaEventQuery(s.done);
-          if (q != cudaErrorNotReady) {
-            const double t = now_seconds();
-            for (size_t i = 0; i < s.jobs.size(); ++i) {
-              if (s.finished[i]) continue;
-              if (__atomic_load_n(s.h_flags + i, __ATOMIC_ACQUIRE) == s.ticket)
-                finish(s, i, s.h_counts + i * 32, POSPOPCNT_OK, t);
-              else
-                finish(s, i, nullptr, q == cudaSuccess ? POSPOPCNT_ERR_CUDA : cuda_fail(q), t);
-            }
+      // every job -- batched or counted alone -- is published through its flag
+      for (size_t i = 0; i < s.jobs.size(); ++i) {
+        if (s.finished[i]) continue;
+        if (__atomic_load_n(s.h_flags + i, __ATOMIC_ACQUIRE) != s.ticket) continue;
+        finish(s, i, s.h_counts + i * 32, POSPOPCNT_OK, now_seconds());
+        any = true;
+      }
+      // watchdog: the slot's stream ran dry (or failed) without publishing every job
+      if (s.remaining && now_seconds() - s.t_launch > 0.5) {
+        const cudaError_t q = cudaStreamQuery(s.stream);
+        if (q != cudaErrorNotReady) {
+          const double t = now_seconds();
+          for (size_t i = 0; i < s.jobs.size(); ++i) {
+            if (s.finished[i]) continue;
+            if (__atomic_load_n(s.h_flags + i, __ATOMIC_ACQUIRE) == s.ticket)
+              finish(s, i, s.h_counts + i * 32, POSPOPCNT_OK, t);
+            else
+              finish(s, i, nullptr, q == cudaSuccess ? POSPOPCNT_ERR_CUDA : cuda_fail(q), t);
           }
+          if (s.single) cudaMemsetAsync(s.d_single, 0, 32 * sizeof(unsigned long long), s.stream);
         }
       }
       if (s.remaining == 0) {
@@ -340,12 +362,32 @@ struct Server {
     return best;
   }
 
-  template <int K>
-  cudaError_t launch_serve(Slot& s, const ServeArgs& args, uint64_t total_words) {
-    const uint64_t tiles = (total_words + args.tile_words - 1) / args.tile_words;
-    serve_kernel<K><<<unsigned(std::max<uint64_t>(1, tiles)), BT_THREADS, 0, s.stream>>>(args);
+  // One batch of m jobs: the job table sized to the batch, then the kernel.
+  template <int K, int CAP>
+  cudaError_t launch_serve(Slot& s, size_t m) {
+    ServeArgs<CAP> args;
+    args.bounds[0] = 0;
+    for (size_t i = 0; i < m; ++i) {
+      args.bounds[i + 1] = args.bounds[i] + int64_t(s.jobs[i].n);
+      args.addr[i] = s.jobs[i].addr;
+    }
+    args.nseg = uint32_t(m);
+    args.ticket = s.ticket;
+    args.tile_words = uint64_t(SERVE_TILE_BYTES / (K / 8));
+    args.rows = s.d_rows;
+    args.pieces = s.d_pieces;
+    args.h_counts = s.dv_counts;
+    args.h_flags = s.dv_flags;
+    const uint64_t total = uint64_t(args.bounds[m]);
+    const uint64_t tiles = (total + args.tile_words - 1) / args.tile_words;
+    serve_kernel<K, CAP><<<unsigned(std::max<uint64_t>(1, tiles)), BT_THREADS, 0, s.stream>>>(args);
     note_launch();
     return cudaGetLastError();
+  }
+
+  template <int K>
+  cudaError_t launch_serve_k(Slot& s, size_t m) {
+    return m <= size_t(SERVE_SMALL_CAP) ? launch_serve<K, SERVE_SMALL_CAP>(s, m) : launch_serve<K, SERVE_MAX_JOBS>(s, m);
   }
 
   int launch(Slot& s, int qi) {
@@ -366,44 +408,36 @@ struct Server {
     s.busy = true;
     cudaError_t e = cudaSuccess;
     int rc = POSPOPCNT_OK;
+    ++s.ticket;
     if (s.single) {
+      // the tuned plain count adds into d_single (zero between jobs); one
+      // warp then publishes it like a batched job: no memset, copy or event
       const Job& j = s.jobs[0];
-      rc = pospopcnt_count(width, POSPOPCNT_KERNEL_AUTO, reinterpret_cast<const void*>(j.addr), size_t(j.n),
-                           reinterpret_cast<uint64_t*>(s.d_single), s.stream);
-      if (rc == POSPOPCNT_OK &&
-          (e = cudaMemcpyAsync(s.h_single, s.d_single, size_t(width) * 8, cudaMemcpyDeviceToHost, s.stream)) !=
-              cudaSuccess)
-        rc = cuda_fail(e);
+      rc = pospopcnt_count_accumulate(width, reinterpret_cast<const void*>(j.addr), size_t(j.n),
+                                      reinterpret_cast<uint64_t*>(s.d_single), s.stream);
+      if (rc == POSPOPCNT_OK) {
+        auto pub = width == 8 ? serve_publish_kernel<8> : width == 16 ? serve_publish_kernel<16>
+                                                                      : serve_publish_kernel<32>;
+        pub<<<1, 32, 0, s.stream>>>(s.d_single, s.dv_counts, s.dv_flags, s.ticket);
+        note_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) rc = cuda_fail(e);
+      }
+      if (rc != POSPOPCNT_OK) cudaMemsetAsync(s.d_single, 0, 32 * sizeof(unsigned long long), s.stream);
     } else {
-      ServeArgs args;
-      args.bounds[0] = 0;
+      // empty jobs have no piece on the device: they complete here
       size_t live = 0;
       for (size_t i = 0; i < m; ++i) {
-        args.bounds[i + 1] = args.bounds[i] + int64_t(s.jobs[i].n);
-        args.addr[i] = s.jobs[i].addr;
         live += s.jobs[i].n > 0;
-      }
-      args.nseg = uint32_t(m);
-      args.ticket = ++s.ticket;
-      args.tile_words = uint64_t(SERVE_TILE_BYTES / (width / 8));
-      args.rows = s.d_rows;
-      args.pieces = s.d_pieces;
-      args.h_counts = s.dv_counts;
-      args.h_flags = s.dv_flags;
-      const uint64_t total = uint64_t(args.bounds[m]);
-      // empty jobs have no piece on the device: they complete here
-      for (size_t i = 0; i < m; ++i)
         if (s.jobs[i].n == 0) {
           static const unsigned long long zeros[32] = {};
           finish(s, i, zeros, POSPOPCNT_OK, now_seconds());
         }
+      }
       if (live) {
-        e = width == 8 ? launch_serve<8>(s, args, total) : width == 16 ? launch_serve<16>(s, args, total)
-                                                                       : launch_serve<32>(s, args, total);
+        e = width == 8 ? launch_serve_k<8>(s, m) : width == 16 ? launch_serve_k<16>(s, m) : launch_serve_k<32>(s, m);
         if (e != cudaSuccess) rc = cuda_fail(e);
       }
     }
-    if (rc == POSPOPCNT_OK && (e = cudaEventRecord(s.done, s.stream)) != cudaSuccess) rc = cuda_fail(e);
     if (rc != POSPOPCNT_OK) {  // fail the unfinished jobs on the host
       const double td = now_seconds();
       for (size_t i = 0; i < m; ++i)
@@ -499,8 +533,8 @@ int pospopcnt_server_create(int device, const pospopcnt_server_config* cfg_in, p
   const size_t rows_bytes = size_t(ppc::SERVE_MAX_JOBS) * 32 * sizeof(uint64_t);
   const size_t pieces_bytes = size_t(ppc::SERVE_MAX_JOBS) * sizeof(unsigned);
   const size_t pieces_pad = ((pieces_bytes + 255) / 256) * 256;
-  const size_t per_slot = rows_bytes + pieces_pad + 256;       // + the single-job row
-  const size_t host_per_slot = rows_bytes + pieces_pad + 256;  // + its host copy
+  const size_t per_slot = rows_bytes + pieces_pad + 256;  // + the single-job row
+  const size_t host_per_slot = rows_bytes + pieces_pad;
   s.slots.resize(size_t(cfg.max_inflight));
   if ((e = cudaMalloc(&s.d_pool, per_slot * s.slots.size())) != cudaSuccess) rc = ppc::cuda_fail(e);
   if (rc == POSPOPCNT_OK && (e = cudaMemset(s.d_pool, 0, per_slot * s.slots.size())) != cudaSuccess)
@@ -522,12 +556,9 @@ int pospopcnt_server_create(int device, const pospopcnt_server_config* cfg_in, p
     char* dvb = static_cast<char*>(dv_pool) + i * host_per_slot;
     sl.h_counts = reinterpret_cast<unsigned long long*>(hb);
     sl.h_flags = reinterpret_cast<unsigned*>(hb + rows_bytes);
-    sl.h_single = reinterpret_cast<unsigned long long*>(hb + rows_bytes + pieces_pad);
     sl.dv_counts = reinterpret_cast<unsigned long long*>(dvb);
     sl.dv_flags = reinterpret_cast<unsigned*>(dvb + rows_bytes);
-    if ((e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming)) != cudaSuccess)
-      rc = ppc::cuda_fail(e);
+    if ((e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking)) != cudaSuccess) rc = ppc::cuda_fail(e);
   }
   cudaSetDevice(prev);
   if (rc != POSPOPCNT_OK) {
@@ -549,7 +580,6 @@ int pospopcnt_server_destroy(pospopcnt_server* srv) {
   cudaSetDevice(s.device);
   for (ppc::Slot& sl : s.slots) {
     if (sl.stream) cudaStreamSynchronize(sl.stream), cudaStreamDestroy(sl.stream);
-    if (sl.done) cudaEventDestroy(sl.done);
   }
   if (s.d_pool) cudaFree(s.d_pool);
   if (s.h_pool) cudaFreeHost(s.h_pool);
@@ -604,6 +634,13 @@ int pospopcnt_server_poll(pospopcnt_server* srv, pospopcnt_result* out, int max,
 int pospopcnt_server_run_trace(pospopcnt_server* srv, size_t n, const double* t_arrival, const int* width,
                                const uint64_t* d_addr, const uint64_t* nwords, double* latency_out,
                                uint64_t* counts_out, int* status_out) {
+  return pospopcnt_server_run_trace_timed(srv, n, t_arrival, width, d_addr, nwords, latency_out, counts_out,
+                                          status_out, nullptr);
+}
+
+int pospopcnt_server_run_trace_timed(pospopcnt_server* srv, size_t n, const double* t_arrival, const int* width,
+                                     const uint64_t* d_addr, const uint64_t* nwords, double* latency_out,
+                                     uint64_t* counts_out, int* status_out, double* stages_out) {
   if (!srv || (n > 0 && (!t_arrival || !width || !d_addr || !nwords || !latency_out)))
     return POSPOPCNT_ERR_INVALID;
   Server& s = srv->impl;
@@ -618,8 +655,11 @@ int pospopcnt_server_run_trace(pospopcnt_server* srv, size_t n, const double* t_
     latency_out[i] = std::nan("");
     if (status_out) status_out[i] = POSPOPCNT_ERR_INVALID;
   }
+  if (stages_out)
+    for (size_t i = 0; i < 3 * n; ++i) stages_out[i] = std::nan("");
   s.trace_counts.store(counts_out);
   s.trace_status.store(status_out);
+  s.trace_stages.store(stages_out);
   s.trace_latency.store(latency_out, std::memory_order_release);
   const uint64_t base = s.total_completed.load(std::memory_order_acquire);
   uint64_t expected = 0;
@@ -657,6 +697,7 @@ int pospopcnt_server_run_trace(pospopcnt_server* srv, size_t n, const double* t_
   s.trace_latency.store(nullptr, std::memory_order_release);
   s.trace_counts.store(nullptr);
   s.trace_status.store(nullptr);
+  s.trace_stages.store(nullptr);
   return POSPOPCNT_OK;
 }
 
