@@ -597,6 +597,36 @@ def run_peaks(args, world, rank, local):
             "nominal_hbm_GBps": 7900.0}
 
 
+def run_latency_floor(args, world, rank, local):
+    """Launch-to-host latency floors of this GPU (the reference points of the
+    serving path): builds and runs paper_1911_02696_gb300/latency_floor.cu."""
+    if rank != 0:
+        return None
+    src = os.path.join(ROOT, "paper_1911_02696_gb300", "latency_floor.cu")
+    out_dir = os.path.join(ROOT, "paper_1911_02696_gb300", "_build")
+    os.makedirs(out_dir, exist_ok=True)
+    exe = os.path.join(out_dir, "latency_floor")
+    subprocess.check_call(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-o", exe, src])
+    res = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    paths = {}
+    status = None
+    for line in res.stdout.splitlines():
+        parts = line.split("|")
+        if parts[0] == "status":
+            status = parts[1:]
+        elif len(parts) == 5:
+            paths[parts[0]] = {"p50_us": float(parts[1]), "p90_us": float(parts[2]), "p99_us": float(parts[3]),
+                               "min_us": float(parts[4])}
+    if res.returncode != 0 or not paths:
+        raise RuntimeError(f"latency_floor failed: rc={res.returncode} {res.stdout[-400:]} {res.stderr[-400:]}")
+    flag = paths["flag kernel, 16 B parameters, host spin"]
+    return {"metric": "launch to host-visible flag latency", "value": flag["p50_us"], "unit": "us",
+            "n_gpus": world, "steps": 2000, "warmup": 2000, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "none (latency probe)",
+            "config": {"workload": "one-block kernels, host timing from the launch call to the result seen"},
+            "paths": paths, "cuda_status": status}
+
+
 def candidate_configs():
     cfgs = [dict(kernel="csa", threads=t, unroll=u) for t in (128, 256, 512) for u in (2, 4, 8)]
     cfgs += [dict(kernel="tma", stages=st, chunk_bytes=c, flags=fl) for st in (2, 3, 4, 6, 8)
@@ -878,7 +908,7 @@ def main(argv=None):
     p.add_argument("--workload", default="u16",
                    choices=["u16", "u16_onehot", "u16_sparse", "u16_misaligned", "u8", "u32", "u64", "popcount", "onehot",
                             "sweep", "batched",
-                            "kernels", "autotune", "serve", "e2e", "peaks"])
+                            "kernels", "autotune", "serve", "e2e", "peaks", "latency_floor"])
     p.add_argument("--batched-nseg", type=int, default=20000)
     p.add_argument("--batched-autotune", action="store_true",
                    help="batched workload: autotune the launch on the layout before timing")
@@ -922,6 +952,8 @@ def main(argv=None):
             out = run_e2e(args, world, rank, local)
         elif args.workload == "peaks":
             out = run_peaks(args, world, rank, local)
+        elif args.workload == "latency_floor":
+            out = run_latency_floor(args, world, rank, local)
         else:
             out = run_plain(args, world, rank, local)
         if world > 1:
