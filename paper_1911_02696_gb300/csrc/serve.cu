@@ -18,7 +18,7 @@
 // are on the GPU join the next batch as soon as a slot and budget free up:
 // batching is continuous, not a queue drained one batch at a time.
 //
-// Device side (serve_kernel): one CTA per 64 KiB tile of the batch's
+// Device side (serve_kernel): one CTA per 32 KiB tile of the batch's
 // virtual word space (short-lived CTAs, so batches on other streams share
 // the SMs at fine grain); each warp counts the pieces of its sub-range (segment helpers shared with the batched kernel) and adds them
 // into the job's row in device memory.  Every warp then bumps the job's
@@ -72,7 +72,11 @@ struct AdmissionPolicy {
 };
 
 constexpr int SERVE_MAX_JOBS = 240;  // job table in the kernel parameters (< 4 KiB)
-constexpr uint64_t SERVE_TILE_BYTES = 64 * 1024;  // one CTA: 8 warps x 8 KiB
+// One CTA: 8 warps x 4 KiB, and a warp's 4 KiB is one trip of its piece
+// counter (32 lanes x 8 vectors): every load of the piece is issued at once,
+// so a cold payload costs one DRAM round trip per warp, not one per trip.
+constexpr int SERVE_VPL = 8;
+constexpr uint64_t SERVE_TILE_BYTES = uint64_t(BT_WARPS) * 32 * SERVE_VPL * 16;  // 32 KiB
 
 // Job table in the kernel parameters, CAP jobs at most: a launch carries
 // only the table size its batch needs (parameters are copied at every launch).
@@ -91,9 +95,10 @@ struct ServeArgs {
   unsigned* h_flags;                   // device view of pinned host memory, SERVE_MAX_JOBS
 };
 
+// Short-lived CTAs: three per SM is enough residency, and leaves each
+// thread the registers of a whole one-trip piece (32 data registers).
 template <int K, int CAP>
-__global__ void __launch_bounds__(BT_THREADS, bt_min_blocks<K>::value)
-    serve_kernel(const __grid_constant__ ServeArgs<CAP> a) {
+__global__ void __launch_bounds__(BT_THREADS, 3) serve_kernel(const __grid_constant__ ServeArgs<CAP> a) {
   constexpr int WB = K / 8;
   constexpr int SH = 5 - ilog2<K>::value;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -115,7 +120,7 @@ __global__ void __launch_bounds__(BT_THREADS, bt_min_blocks<K>::value)
       const int64_t pb = seg_hi < w1 ? seg_hi : w1;
       if (pa < pb) {
         const uint8_t* pbase = reinterpret_cast<const uint8_t*>(a.addr[s] - uint64_t(seg_lo) * WB);
-        const uint32_t v = warp_piece_counts<K>(pbase, uint64_t(pa), uint64_t(pb));
+        const uint32_t v = warp_piece_counts<K, SERVE_VPL>(pbase, uint64_t(pa), uint64_t(pb));
         unsigned long long* row = a.rows + s * 32;
         if ((lane & ((1 << SH) - 1)) == 0 && v) atomicAdd(row + (lane >> SH), (unsigned long long)v);
         // the warp that adds the job's last piece publishes its counts
