@@ -205,6 +205,10 @@ def make_input(kind: str, seed: int, log2_words: int | None = None, limit: int |
                          lambda m: synth.uniform_bytes(seed, m)),
             "onehot": (-16, f"fused one-hot encode + count: 2^{log2_words} u8 ids, Zipf(1.1) over 16 categories",
                        lambda m: synth.categorical_ids(seed, m, zipf16, np.uint8)),
+            "onehot_u16ids": (-16, f"fused one-hot encode + count: 2^{log2_words} u16 ids, Zipf(1.1) over 16 "
+                                   "categories", lambda m: synth.categorical_ids(seed, m, zipf16, np.uint16)),
+            "onehot_u32ids": (-16, f"fused one-hot encode + count: 2^{log2_words} u32 ids, Zipf(1.1) over 16 "
+                                   "categories", lambda m: synth.categorical_ids(seed, m, zipf16, np.uint32)),
         }
         width = {"u8": 8, "u32": 32, "u64": 64}.get(kind, 16)
         width, desc, gen = table.get(kind, (width, f"pospopcnt_u{width} n=2^{log2_words} uniform random bits",
@@ -224,6 +228,12 @@ def make_input(kind: str, seed: int, log2_words: int | None = None, limit: int |
                lambda m: synth.uniform_bits(seed, m, 8)),
         "onehot": (1 << 31, -16, 0, "fused one-hot encode + count: 2^31 u8 ids, Zipf(1.1) over 16 categories (2 GiB)",
                    lambda m: synth.categorical_ids(seed, m, zipf16, np.uint8)),
+        "onehot_u16ids": (1 << 30, -16, 0,
+                          "fused one-hot encode + count: 2^30 u16 ids, Zipf(1.1) over 16 categories (2 GiB)",
+                          lambda m: synth.categorical_ids(seed, m, zipf16, np.uint16)),
+        "onehot_u32ids": (1 << 29, -16, 0,
+                          "fused one-hot encode + count: 2^29 u32 ids, Zipf(1.1) over 16 categories (2 GiB)",
+                          lambda m: synth.categorical_ids(seed, m, zipf16, np.uint32)),
         "popcount": (1 << 31, 1, 0, "array popcount of 2 GiB of uniform random bits",
                      lambda m: synth.uniform_bytes(seed, m)),
         "u64": (1 << 28, 64, 0, "pospopcnt_u64 n=2^28 uniform random bits (2 GiB)",
@@ -308,8 +318,10 @@ def run_plain(args, world, rank, local):
     counts = torch.empty(onehot_k or width, dtype=torch.int64, device=dev)
     ppc.pospopcnt_init(local)
     if onehot_k:
+        id_dtype = {1: torch.uint8, 2: torch.int16, 4: torch.int32}[words.itemsize]
+
         def fn(t, counts):
-            return ppc.pospopcnt_onehot_counts(t, onehot_k, counts=counts)
+            return ppc.pospopcnt_onehot_counts(t.view(id_dtype), onehot_k, counts=counts)
     elif args.kernel:  # a named kernel family in its default configuration (comparison / profiling)
         fixed = {"kernel": args.kernel}
 
@@ -376,11 +388,17 @@ def run_plain(args, world, rank, local):
     if onehot_k:
         cfg, kname = {"kernel": "onehot", "k": onehot_k}, "onehot"
         lw = 8 if onehot_k <= 8 else 16 if onehot_k <= 16 else 32
-        kernel_label = (f"onehot_ring_kernel<{lw}>" if nbytes >= (32 << 20) else f"onehot_lut_kernel<{lw}, 256>") \
-            + f" (8-bit ids, k = {onehot_k})"
+        idb = words.itemsize
+        if idb <= 2:
+            kernel_label = (f"onehot_ring_kernel<{lw}, {idb}>" if nbytes >= (32 << 20) else
+                            f"onehot_lut_kernel<{lw}, {idb}, 256>") + f" ({8 * idb}-bit ids, k = {onehot_k})"
+        else:
+            kernel_label = f"onehot_kernel<{idb}, {lw}, 256> ({8 * idb}-bit ids, k = {onehot_k})"
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_source": f"{peak_src} (copy bandwidth)",
-                "traffic": profiled_traffic(f"onehot_k{onehot_k}" if onehot_k else f"{kname}_u{width}", nbytes),
+                "traffic": profiled_traffic((f"onehot_k{onehot_k}" if words.itemsize == 1 else
+                                             f"onehot{8 * words.itemsize}_k{onehot_k}") if onehot_k
+                                            else f"{kname}_u{width}", nbytes),
                 "kernel": f"{kernel_label} (+ a {counts_bytes}-byte memset)"}
     out = None
     if rank == 0:
@@ -850,7 +868,8 @@ def run_e2e(args, world, rank, local):
             "frac_of_link": round(res["pinned_in_place_GBps"] / res["memcpy_pinned_GBps"], 4)}
 
 
-REFERENCE_WORKLOADS = ("u16", "u16_onehot", "u16_sparse", "u16_misaligned", "u8", "u32", "u64", "popcount", "onehot")
+REFERENCE_WORKLOADS = ("u16", "u16_onehot", "u16_sparse", "u16_misaligned", "u8", "u32", "u64", "popcount", "onehot",
+                       "onehot_u16ids", "onehot_u32ids")
 
 
 def run_reference(args, world, rank):
@@ -907,7 +926,7 @@ def main(argv=None):
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="u16",
                    choices=["u16", "u16_onehot", "u16_sparse", "u16_misaligned", "u8", "u32", "u64", "popcount", "onehot",
-                            "sweep", "batched",
+                            "onehot_u16ids", "onehot_u32ids", "sweep", "batched",
                             "kernels", "autotune", "serve", "e2e", "peaks", "latency_floor"])
     p.add_argument("--batched-nseg", type=int, default=20000)
     p.add_argument("--batched-autotune", action="store_true",

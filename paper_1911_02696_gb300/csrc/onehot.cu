@@ -189,6 +189,49 @@ __device__ __forceinline__ void encode_word(uint32_t* r, uint32_t w, LutRef<IMM>
   }
 }
 
+// 16-bit ids: each 16-bit half of w clamped to at most 255 (one instruction
+// for both), so that any id >= 256 reads table row 255, which is empty
+// (k <= 32); an id below 256 keeps its low byte.
+__device__ __forceinline__ uint32_t clamp_ids16(uint32_t w) {
+  uint32_t d;
+  asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(w), "r"(0x00FF00FFu));
+  return d;
+}
+
+// Encoded registers of the 16 bytes of ids in x (IDB bytes per id): 16/IDB
+// ids, 32/LW per register.
+template <int LW, int IDB, uint32_t IMM>
+__device__ __forceinline__ void encode_vec(uint32_t* d, const uint4& x, LutRef<IMM> t, uint32_t lanebase,
+                                           uint32_t one) {
+  const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+  if constexpr (IDB == 1) {
+    constexpr int RPW = 4 / (32 / LW);  // registers per word of 4 ids
+#pragma unroll
+    for (int q = 0; q < 4; ++q) encode_word<LW, IMM>(d + q * RPW, w[q], t, lanebase, one);
+  } else {
+    // two ids per word: bytes 0 and 2 of the clamped word are their rows
+    uint32_t p[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t c = clamp_ids16(w[q]);
+      const uint32_t off0 = __byte_perm(c, lanebase, 0x7604u), off1 = __byte_perm(c, lanebase, 0x7624u);
+      if constexpr (LW == 32) {
+        d[2 * q] = t.template at<0>(off0);
+        d[2 * q + 1] = t.template at<0>(off1);
+      } else {
+        p[q] = mad_one(t.template at<128>(off1), one, t.template at<0>(off0));
+      }
+    }
+    if constexpr (LW == 16) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) d[q] = p[q];
+    } else if constexpr (LW == 8) {  // p holds its two ids in bytes 0, 1 (and 2, 3)
+      d[0] = __byte_perm(p[0], p[1], 0x7610u);
+      d[1] = __byte_perm(p[2], p[3], 0x7610u);
+    }
+  }
+}
+
 // flush() with the additions on the FMA pipe.
 template <int K>
 __device__ __forceinline__ void flush_mad(uint32_t (&top)[K], uint32_t t, uint32_t one) {
@@ -245,21 +288,21 @@ struct PairedCounts {
   }
 };
 
-// Circuit over 2^N registers per trip: F_5, or F_4 for 8-bit lanes (four
-// ids per register, so 16 registers already hold 64 ids).
-template <int LW>
+// A trip is U = 4 vectors per thread (2 for one 8-bit id per register),
+// through the circuit F_N over their R = 2^N registers (N <= 5).
+template <int LW, int IDB>
 struct LutTrip {
-  static constexpr int REGS_PER_VEC = 16 / (32 / LW);  // 16 ids per vector
-  static constexpr int N = LW == 8 ? 4 : 5;
+  static constexpr int REGS_PER_VEC = (16 / IDB) / (32 / LW);
+  static constexpr int N = ilog2<4 * REGS_PER_VEC>::value < 5 ? ilog2<4 * REGS_PER_VEC>::value : 5;
   static constexpr int R = 1 << N;
   static constexpr int U = R / REGS_PER_VEC;  // vectors per trip
 };
 
 // The thread's share of the body: whole trips, then at most one partial trip.
-template <int LW, int NTHREADS, uint32_t IMM>
+template <int LW, int IDB, int NTHREADS, uint32_t IMM>
 __device__ __forceinline__ void lut_count_body(const OnehotArgs& a, LutRef<IMM> t, uint32_t lanebase,
-                                               PairedCounts<LW, LutTrip<LW>::N>& acc) {
-  constexpr int REGS_PER_VEC = LutTrip<LW>::REGS_PER_VEC, R = LutTrip<LW>::R, U = LutTrip<LW>::U;
+                                               PairedCounts<LW, LutTrip<LW, IDB>::N>& acc) {
+  constexpr int REGS_PER_VEC = LutTrip<LW, IDB>::REGS_PER_VEC, R = LutTrip<LW, IDB>::R, U = LutTrip<LW, IDB>::U;
   const uint32_t one = a.one;
   const uint64_t stride = uint64_t(gridDim.x) * NTHREADS;
   const uint64_t span = uint64_t(U - 1) * stride;
@@ -279,26 +322,20 @@ __device__ __forceinline__ void lut_count_body(const OnehotArgs& a, LutRef<IMM> 
     uint32_t d[R];
 #pragma unroll
     for (int i = 0; i < U; ++i) {
-      const uint32_t w[4] = {x[i].x, x[i].y, x[i].z, x[i].w};
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        encode_word<LW, IMM>(d + i * REGS_PER_VEC + j * (REGS_PER_VEC / 4), w[j], t, lanebase, one);
+      encode_vec<LW, IDB, IMM>(d + i * REGS_PER_VEC, x[i], t, lanebase, one);
       if (full_n) x[i] = ld_stream(a.body + vn + i * stride);
     }
     acc.add_trip(d, one);
     v = vn;
     full = full_n;
   }
-  if (v < a.nvec) {  // last, partial trip: a missing vector reads as ids 255, which encode to nothing
+  if (v < a.nvec) {  // last, partial trip: a missing vector reads as all-ones ids, which encode to nothing
     uint32_t d[R];
 #pragma unroll
     for (int i = 0; i < U; ++i) {
       const uint64_t idx = v + i * stride;
       const uint4 y = idx < a.nvec ? ld_stream(a.body + idx) : make_uint4(~0u, ~0u, ~0u, ~0u);
-      const uint32_t w[4] = {y.x, y.y, y.z, y.w};
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        encode_word<LW, IMM>(d + i * REGS_PER_VEC + j * (REGS_PER_VEC / 4), w[j], t, lanebase, one);
+      encode_vec<LW, IDB, IMM>(d + i * REGS_PER_VEC, y, t, lanebase, one);
     }
     acc.add_trip(d, one);
   }
@@ -309,10 +346,10 @@ __device__ __forceinline__ void lut_count_body(const OnehotArgs& a, LutRef<IMM> 
 // The kernel checks it at run time and adds the address itself otherwise.
 constexpr uint32_t LUT_USUAL_BASE = 1024;
 
-template <int LW, int NTHREADS>
+template <int LW, int IDB, int NTHREADS>
 __global__ void __launch_bounds__(NTHREADS, 3) onehot_lut_kernel(OnehotArgs a) {
   extern __shared__ __align__(1024) uint8_t lut[];  // the only shared memory of this kernel
-  constexpr int N = LutTrip<LW>::N;
+  constexpr int N = LutTrip<LW, IDB>::N;
   const uint32_t lane = threadIdx.x & 31u;
   for (uint32_t e = threadIdx.x >> 5; e < 256u; e += NTHREADS / 32) {
     *reinterpret_cast<uint32_t*>(lut + e * LUT_ROW + lane * 4u) = lut_lo<LW>(e, a.k);
@@ -326,19 +363,19 @@ __global__ void __launch_bounds__(NTHREADS, 3) onehot_lut_kernel(OnehotArgs a) {
   const uint32_t base = static_cast<uint32_t>(__cvta_generic_to_shared(lut));
   PairedCounts<LW, N> acc;
   if (base == LUT_USUAL_BASE)
-    lut_count_body<LW, NTHREADS, LUT_USUAL_BASE>(a, LutRef<LUT_USUAL_BASE>{base}, lanebase, acc);
+    lut_count_body<LW, IDB, NTHREADS, LUT_USUAL_BASE>(a, LutRef<LUT_USUAL_BASE>{base}, lanebase, acc);
   else
-    lut_count_body<LW, NTHREADS, 0>(a, LutRef<0>{base}, lanebase, acc);
+    lut_count_body<LW, IDB, NTHREADS, 0>(a, LutRef<0>{base}, lanebase, acc);
   uint32_t c[LW];
   acc.finish(c);
   if (blockIdx.x == 0) {  // head and tail ids (fewer than 16 each), one by one
     const unsigned t = threadIdx.x;
     if (t < a.head_ids) {
-      const uint32_t id = a.head[t];
+      const uint32_t id = load_id<IDB>(a.head + t * IDB);
       count_word<LW>(c, id < a.k ? 1u << id : 0u);
     }
     if (t >= 32 && t - 32 < a.tail_ids) {
-      const uint32_t id = a.tail[t - 32];
+      const uint32_t id = load_id<IDB>(a.tail + (t - 32) * IDB);
       count_word<LW>(c, id < a.k ? 1u << id : 0u);
     }
   }
@@ -361,12 +398,13 @@ __global__ void __launch_bounds__(NTHREADS, 3) onehot_lut_kernel(OnehotArgs a) {
   }
 }
 
-template <int LW>
+template <int LW, int IDB>
 static int launch_onehot_lut(const DeviceState& st, OnehotArgs a, cudaStream_t stream) {
   constexpr int T = 256;
-  constexpr int U = LutTrip<LW>::U;
-  auto kern = onehot_lut_kernel<LW, T>;
-  if (const cudaError_t e = ensure_dynamic_smem<onehot_lut_kernel<LW, T>>(st.device, LUT_BYTES)) return cuda_fail(e);
+  constexpr int U = LutTrip<LW, IDB>::U;
+  auto kern = onehot_lut_kernel<LW, IDB, T>;
+  if (const cudaError_t e = ensure_dynamic_smem<onehot_lut_kernel<LW, IDB, T>>(st.device, LUT_BYTES))
+    return cuda_fail(e);
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, T, LUT_BYTES) != cudaSuccess || occ < 1) occ = 1;
   const uint64_t cap = uint64_t(st.sms) * uint64_t(occ);
@@ -412,20 +450,18 @@ constexpr uint64_t RING_MIN_BYTES = uint64_t(32) << 20;
 
 // One trip over vectors [base, base + U*CT) of a ring stage; GUARD: some may
 // lie past nv (the partial last chunk of the input) and read as ids 255.
-template <int LW, uint32_t IMM, bool GUARD>
+template <int LW, int IDB, uint32_t IMM, bool GUARD>
 __device__ __forceinline__ void ring_trip(const uint4* sv, uint32_t base, uint32_t nv, LutRef<IMM> t,
-                                          uint32_t lanebase, uint32_t one, PairedCounts<LW, LutTrip<LW>::N>& acc) {
-  constexpr int REGS_PER_VEC = LutTrip<LW>::REGS_PER_VEC, R = LutTrip<LW>::R, U = LutTrip<LW>::U;
+                                          uint32_t lanebase, uint32_t one,
+                                          PairedCounts<LW, LutTrip<LW, IDB>::N>& acc) {
+  constexpr int REGS_PER_VEC = LutTrip<LW, IDB>::REGS_PER_VEC, R = LutTrip<LW, IDB>::R, U = LutTrip<LW, IDB>::U;
   constexpr uint32_t CT = RING_CWARPS * 32;
   uint32_t d[R];
 #pragma unroll
   for (int j = 0; j < U; ++j) {
     const uint32_t idx = base + j * CT + threadIdx.x;
-    const uint4 y = (!GUARD || idx < nv) ? sv[idx] : make_uint4(~0u, ~0u, ~0u, ~0u);
-    const uint32_t w[4] = {y.x, y.y, y.z, y.w};
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      encode_word<LW, IMM>(d + j * REGS_PER_VEC + q * (REGS_PER_VEC / 4), w[q], t, lanebase, one);
+    const uint4 y = (!GUARD || idx < nv) ? sv[idx] : make_uint4(~0u, ~0u, ~0u, ~0u);  // all-ones ids: nothing
+    encode_vec<LW, IDB, IMM>(d + j * REGS_PER_VEC, y, t, lanebase, one);
   }
   acc.add_trip(d, one);
 }
@@ -433,11 +469,11 @@ __device__ __forceinline__ void ring_trip(const uint4* sv, uint32_t base, uint32
 // The consumer warps' loop over this CTA's chunks; returns the chunks it
 // finished.  A wait that runs out sets the error word and ends the loop (the
 // producer's own bounded waits end it there).
-template <int LW, uint32_t IMM>
+template <int LW, int IDB, uint32_t IMM>
 __device__ __forceinline__ uint32_t ring_consume(const OnehotArgs& a, const uint8_t* ring, RingCtl* ctl,
                                                  uint32_t my_chunks, LutRef<IMM> t, uint32_t lanebase,
-                                                 PairedCounts<LW, LutTrip<LW>::N>& acc) {
-  constexpr uint32_t TRIP = LutTrip<LW>::U * RING_CWARPS * 32;  // vectors per trip; divides a chunk
+                                                 PairedCounts<LW, LutTrip<LW, IDB>::N>& acc) {
+  constexpr uint32_t TRIP = LutTrip<LW, IDB>::U * RING_CWARPS * 32;  // vectors per trip; divides a chunk
   constexpr uint32_t CV = RING_CHUNK / 16;                       // vectors per chunk
   const uint32_t one = a.one, lane = threadIdx.x & 31u;
   // Only the input's last chunk can be partial; it is this CTA's last chunk
@@ -461,10 +497,10 @@ __device__ __forceinline__ uint32_t ring_consume(const OnehotArgs& a, const uint
     if (i < full_chunks) {
 #pragma unroll
       for (uint32_t base = 0; base < CV; base += TRIP)
-        ring_trip<LW, IMM, false>(sv, base, CV, t, lanebase, one, acc);
+        ring_trip<LW, IDB, IMM, false>(sv, base, CV, t, lanebase, one, acc);
     } else {
       const uint32_t nv = uint32_t(body_bytes % RING_CHUNK) / 16u;
-      for (uint32_t base = 0; base < nv; base += TRIP) ring_trip<LW, IMM, true>(sv, base, nv, t, lanebase, one, acc);
+      for (uint32_t base = 0; base < nv; base += TRIP) ring_trip<LW, IDB, IMM, true>(sv, base, nv, t, lanebase, one, acc);
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&ctl->empty[s]);
@@ -476,13 +512,13 @@ __device__ __forceinline__ uint32_t ring_consume(const OnehotArgs& a, const uint
   return i;
 }
 
-template <int LW>
+template <int LW, int IDB>
 __global__ void __launch_bounds__(RING_THREADS, 1) onehot_ring_kernel(OnehotArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];  // the only shared memory of this kernel
   uint8_t* lut = smem;
   const uint8_t* ring = smem + LUT_BYTES;
   RingCtl* ctl = reinterpret_cast<RingCtl*>(smem + LUT_BYTES + size_t(RING_STAGES) * RING_CHUNK);
-  constexpr int N = LutTrip<LW>::N;
+  constexpr int N = LutTrip<LW, IDB>::N;
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   const uint64_t body_bytes = a.nvec * 16;
   const uint64_t nchunks = (body_bytes + RING_CHUNK - 1) / RING_CHUNK;
@@ -535,8 +571,9 @@ __global__ void __launch_bounds__(RING_THREADS, 1) onehot_ring_kernel(OnehotArgs
     PairedCounts<LW, N> acc;
     const uint32_t done =
         base == LUT_USUAL_BASE
-            ? ring_consume<LW, LUT_USUAL_BASE>(a, ring, ctl, my_chunks, LutRef<LUT_USUAL_BASE>{base}, lanebase, acc)
-            : ring_consume<LW, 0>(a, ring, ctl, my_chunks, LutRef<0>{base}, lanebase, acc);
+            ? ring_consume<LW, IDB, LUT_USUAL_BASE>(a, ring, ctl, my_chunks, LutRef<LUT_USUAL_BASE>{base},
+                                                    lanebase, acc)
+            : ring_consume<LW, IDB, 0>(a, ring, ctl, my_chunks, LutRef<0>{base}, lanebase, acc);
     if (lane == 0) ctl->consumed[warp] = done;
     acc.finish(c);
   }
@@ -556,11 +593,11 @@ __global__ void __launch_bounds__(RING_THREADS, 1) onehot_ring_kernel(OnehotArgs
   if (blockIdx.x == 0) {  // head and tail ids (fewer than 16 each), one by one
     const unsigned t = threadIdx.x;
     if (t < a.head_ids) {
-      const uint32_t id = a.head[t];
+      const uint32_t id = load_id<IDB>(a.head + t * IDB);
       count_word<LW>(c, id < a.k ? 1u << id : 0u);
     }
     if (t >= 32 && t - 32 < a.tail_ids) {
-      const uint32_t id = a.tail[t - 32];
+      const uint32_t id = load_id<IDB>(a.tail + (t - 32) * IDB);
       count_word<LW>(c, id < a.k ? 1u << id : 0u);
     }
   }
@@ -582,10 +619,10 @@ __global__ void __launch_bounds__(RING_THREADS, 1) onehot_ring_kernel(OnehotArgs
   }
 }
 
-template <int LW>
+template <int LW, int IDB>
 static int launch_onehot_ring(const DeviceState& st, OnehotArgs a, cudaStream_t stream) {
-  auto kern = onehot_ring_kernel<LW>;
-  if (const cudaError_t e = ensure_dynamic_smem<onehot_ring_kernel<LW>>(st.device, int(RING_SMEM)))
+  auto kern = onehot_ring_kernel<LW, IDB>;
+  if (const cudaError_t e = ensure_dynamic_smem<onehot_ring_kernel<LW, IDB>>(st.device, int(RING_SMEM)))
     return cuda_fail(e);
   const uint64_t nchunks = (a.nvec * 16 + RING_CHUNK - 1) / RING_CHUNK;
   uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(uint64_t(st.sms), nchunks));
@@ -626,15 +663,15 @@ static int launch_onehot(const DeviceState& st, OnehotArgs a, cudaStream_t strea
 
 template <int IDB>
 static int launch_onehot_idb(const DeviceState& st, const OnehotArgs& a, cudaStream_t stream) {
-  if constexpr (IDB == 1) {
+  if constexpr (IDB <= 2) {
     if (a.nvec * 16 >= RING_MIN_BYTES) {  // enough chunks to give every SM several
-      if (a.k <= 8) return launch_onehot_ring<8>(st, a, stream);
-      if (a.k <= 16) return launch_onehot_ring<16>(st, a, stream);
-      return launch_onehot_ring<32>(st, a, stream);
+      if (a.k <= 8) return launch_onehot_ring<8, IDB>(st, a, stream);
+      if (a.k <= 16) return launch_onehot_ring<16, IDB>(st, a, stream);
+      return launch_onehot_ring<32, IDB>(st, a, stream);
     }
-    if (a.k <= 8) return launch_onehot_lut<8>(st, a, stream);
-    if (a.k <= 16) return launch_onehot_lut<16>(st, a, stream);
-    return launch_onehot_lut<32>(st, a, stream);
+    if (a.k <= 8) return launch_onehot_lut<8, IDB>(st, a, stream);
+    if (a.k <= 16) return launch_onehot_lut<16, IDB>(st, a, stream);
+    return launch_onehot_lut<32, IDB>(st, a, stream);
   } else {
     if (a.k <= 8) return launch_onehot<IDB, 8>(st, a, stream);
     if (a.k <= 16) return launch_onehot<IDB, 16>(st, a, stream);

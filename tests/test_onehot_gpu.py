@@ -70,18 +70,37 @@ def test_u8_every_id_value(k):
         assert np.array_equal(_run(ids, k, int(rng.integers(0, 16))), oracle.onehot_counts(ids, k)), n
 
 
+@pytest.mark.parametrize("idb", [1, 2])
 @pytest.mark.parametrize("k", [3, 8, 16, 17, 32])
-def test_u8_bulk_copy_sizes(k):
-    """8-bit ids from 32 MiB up go through bulk copies into a shared-memory
-    ring: the exact threshold, a ragged chunk count, a partial last chunk
-    at an odd start, ids over all 256 values and skewed ids."""
-    rng = np.random.default_rng(100 + k)
+def test_bulk_copy_sizes(idb, k):
+    """8- and 16-bit ids from 32 MiB up go through bulk copies into a
+    shared-memory ring: the exact threshold, a ragged chunk count, a partial
+    last chunk at an odd start, ids over the whole id range and skewed ids."""
+    rng = np.random.default_rng(100 + k + 1000 * idb)
+    top = 256 if idb == 1 else 65536
     sizes = [(32 << 20, 0), ((32 << 20) - 16, 0), (152 * 32768 * 7 + 16 * 100 + 3, 5), ((40 << 20) + 17, 3)]
-    for n, off in sizes:
-        ids = rng.integers(0, 256, size=n).astype(np.uint8)
-        assert np.array_equal(_run(ids, k, off), oracle.onehot_counts(ids, k)), (n, off)
-    ids = synth.categorical_ids(k, (48 << 20) + 9, synth.zipf_cdf(min(2 * k, 64)), np.uint8)
-    assert np.array_equal(_run(ids, k, 1), oracle.onehot_counts(ids, k))
+    for nbytes, off in sizes:
+        n = nbytes // idb
+        ids = rng.integers(0, top, size=n).astype(DT[idb])
+        assert np.array_equal(_run(ids, k, off - off % idb), oracle.onehot_counts(ids, k)), (n, off)
+    ids = synth.categorical_ids(k, ((48 << 20) + 9) // idb, synth.zipf_cdf(min(2 * k, 64)), DT[idb])
+    assert np.array_equal(_run(ids, k, idb), oracle.onehot_counts(ids, k))
+
+
+@pytest.mark.parametrize("k", [1, 8, 16, 32])
+def test_u16_ids_with_high_bytes(k):
+    """16-bit ids whose low byte is a valid category but whose high byte is
+    not zero (257, 0x1F01, 0xFF00 + j, 0xFFFF) must count nowhere; mixed
+    with valid ids, at sizes for both 16-bit-id kernels."""
+    rng = np.random.default_rng(7 + k)
+    decoys = np.array([256 + j for j in range(32)] + [0x1F00 + j for j in range(32)] +
+                      [0xFF00 + j for j in range(32)] + [0xFFFF, 0x8000, 0x0100], dtype=np.uint16)
+    for n in (1000, 3 * (1 << 20) + 5, (20 << 20) + 3):
+        valid = rng.integers(0, k, size=n).astype(np.uint16)
+        ids = np.where(rng.random(n) < 0.5, valid, decoys[rng.integers(0, decoys.size, size=n)]).astype(np.uint16)
+        got = _run(ids, k, 2 * int(rng.integers(0, 8)))
+        assert np.array_equal(got, oracle.onehot_counts(ids, k)), n
+        assert int(got.sum()) == int(np.sum(ids < k))
 
 
 def test_rejects():
