@@ -446,6 +446,23 @@ def run_sweep(args, world, rank, local):
     stream = torch.cuda.current_stream(dev)
     points = []
     big = torch.from_numpy(synth.uniform_bytes(rank, 4 << 30)).to(dev)
+
+    def device_us(fn, reps=50):
+        ts = []
+        for _ in range(reps):
+            torch.cuda._sleep(200000)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b) * 1e3)
+        return round(statistics.median(ts), 2)
+
+    # floors measured the same way: nothing between the events, and one
+    # near-empty kernel (torch's spin kernel asked for 0 cycles)
+    floors = {"events_only_us": device_us(lambda: None), "empty_kernel_us": device_us(lambda: torch.cuda._sleep(0)),
+              "memset_128B_us": device_us(lambda: counts.zero_())}
     for e in range(5, 17):
         nbytes = 1 << (2 * e)
         x = big[:nbytes]
@@ -476,7 +493,7 @@ def run_sweep(args, world, rank, local):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
             "config": {"workload": "u16 size sweep 1 KiB..4 GiB, powers of 4", "l2_bytes": l2},
-            "points": points}
+            "floors": floors, "points": points}
 
 
 def run_batched(args, world, rank, local):
