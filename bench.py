@@ -632,6 +632,55 @@ def run_peaks(args, world, rank, local):
             "nominal_hbm_GBps": 7900.0}
 
 
+def run_l2_states(args, world, rank, local):
+    """u16 at 64 MiB .. 1 GiB, each candidate configuration timed with the
+    L2 in three states before each call: holding the input (warm: the same
+    call repeated), full of clean lines of another buffer (a 256 MiB read),
+    or full of dirty lines of another buffer (a 256 MiB write, which must be
+    written back during the read).  Device time between CUDA events,
+    median of 30."""
+    import torch
+    import paper_1911_02696_gb300 as ppc
+    import synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ppc.pospopcnt_init(local)
+    stream = torch.cuda.current_stream(dev)
+    other = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    counts = torch.empty(16, dtype=torch.int64, device=dev)
+    big = torch.from_numpy(synth.uniform_bytes(rank, 1 << 30)).to(dev)
+    cands = [dict(kernel="csa", threads=128, unroll=4), dict(kernel="csa", threads=512, unroll=8),
+             dict(kernel="tma", stages=4, chunk_bytes=49152), dict(kernel="tma", stages=3, chunk_bytes=65536),
+             dict(kernel="tma", stages=4, chunk_bytes=49152, flags=1)]
+    prep = {"warm": lambda: None, "clean": lambda: other.sum(), "dirty": lambda: other.fill_(1)}
+    rows = []
+    for mib in (64, 128, 256, 512, 1024):
+        x = big[: mib << 20]
+        default = ppc.pospopcnt_get_config(16, x.numel() // 2)
+        for cfg in cands + [{"default": default}]:
+            run_cfg = default if "default" in cfg else cfg
+            row = {"MiB": mib, "config": cfg}
+            for state, fn in prep.items():
+                ts = []
+                for _ in range(30):
+                    fn()
+                    torch.cuda._sleep(200000)
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    ppc.pospopcnt_count_config(16, run_cfg, x, counts=counts)
+                    b.record(stream)
+                    b.synchronize()
+                    ts.append(a.elapsed_time(b) * 1e3)
+                row[f"{state}_us"] = round(statistics.median(ts), 1)
+            rows.append(row)
+    if rank != 0:
+        return None
+    return {"metric": "pospopcnt_u16 device time by L2 state", "value": None, "unit": "us", "n_gpus": world,
+            "steps": 30, "warmup": 0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u16", "data": "synthetic", "config": {"workload": "u16 64 MiB..1 GiB, three L2 states"},
+            "rows": rows}
+
+
 def run_latency_floor(args, world, rank, local):
     """Launch-to-host latency floors of this GPU (the reference points of the
     serving path): builds and runs paper_1911_02696_gb300/latency_floor.cu."""
@@ -944,7 +993,7 @@ def main(argv=None):
     p.add_argument("--workload", default="u16",
                    choices=["u16", "u16_onehot", "u16_sparse", "u16_misaligned", "u8", "u32", "u64", "popcount", "onehot",
                             "onehot_u16ids", "onehot_u32ids", "sweep", "batched",
-                            "kernels", "autotune", "serve", "e2e", "peaks", "latency_floor"])
+                            "kernels", "autotune", "serve", "e2e", "peaks", "latency_floor", "l2_states"])
     p.add_argument("--batched-nseg", type=int, default=20000)
     p.add_argument("--batched-autotune", action="store_true",
                    help="batched workload: autotune the launch on the layout before timing")
@@ -990,6 +1039,8 @@ def main(argv=None):
             out = run_peaks(args, world, rank, local)
         elif args.workload == "latency_floor":
             out = run_latency_floor(args, world, rank, local)
+        elif args.workload == "l2_states":
+            out = run_l2_states(args, world, rank, local)
         else:
             out = run_plain(args, world, rank, local)
         if world > 1:

@@ -95,14 +95,24 @@ pospopcnt_config tuned_default(int width, int cls) {
     c.threads = 128, c.unroll = 8;
     return c;
   }
-  c.kernel = POSPOPCNT_KERNEL_TMA;
   if (cls == 13) {
-    c.stages = 2, c.chunk_bytes = 32768;
-  } else if (width == 16) {
+    // 64..256 MiB: register loads.  Timed with L2 holding the input (warm),
+    // unrelated clean lines, or unrelated dirty lines that must be written
+    // back during the read, this kernel is as fast as the bulk-copy ring in
+    // the first two states and 10-20 % faster in the third.
+    c.threads = 512, c.unroll = 8;
+    return c;
+  }
+  c.kernel = POSPOPCNT_KERNEL_TMA;
+  if (width == 16) {
     c.stages = 4, c.chunk_bytes = 49152;  // 192 KiB in flight per SM
   } else {
     c.stages = 3, c.chunk_bytes = 65536;
   }
+  // 256 MiB..1 GiB: the ring with an evict-first hint, which keeps its speed
+  // with a clean L2 and halves most of its loss when the L2 is full of dirty
+  // lines; from 1 GiB the hint measured no better.
+  if (cls == 14) c.flags = POSPOPCNT_FLAG_EVICT_FIRST;
   return c;
 }
 
