@@ -118,6 +118,23 @@ def test_argument_checks_need_no_device():
     assert lib.pospopcnt_batched(good, good, 3, 64, good, None) == 1
     assert lib.pospopcnt_batched(P((1 << 20) + 1), good, 3, 16, good, None) == 2
     assert lib.pospopcnt_batched(good, P((1 << 20) + 4), 3, 16, good, None) == 2
+    # batched launch configuration: bad width, out-of-range fields, null outputs
+    cfg = ppc.BatchedConfig(16384, 0)
+    assert lib.pospopcnt_batched_get_config(12, ctypes.byref(cfg)) == 1
+    assert lib.pospopcnt_batched_get_config(16, None) == 1
+    for unit, bps in ((2048, 0), (4096 + 64, 0), (2 << 20, 0), (4096, -1), (4096, 33)):
+        bad = ppc.BatchedConfig(unit, bps)
+        assert lib.pospopcnt_batched_set_config(16, ctypes.byref(bad)) == 1, (unit, bps)
+    assert lib.pospopcnt_batched_set_config(64, None) == 1
+    assert lib.pospopcnt_batched_autotune(good, good, 3, 16, good, None, None, None) == 1
+    assert lib.pospopcnt_batched_autotune(good, good, 0, 16, good, ctypes.byref(cfg), None, None) == 1
+    # one-hot counts: id width, k range, alignment
+    assert lib.pospopcnt_onehot_counts(good, 5, 3, 16, good, None) == 1
+    assert lib.pospopcnt_onehot_counts(good, 5, 1, 0, good, None) == 1
+    assert lib.pospopcnt_onehot_counts(good, 5, 1, 33, good, None) == 1
+    assert lib.pospopcnt_onehot_counts(P((1 << 20) + 1), 5, 2, 16, good, None) == 2
+    # serving: null server / outputs
+    assert lib.pospopcnt_server_run_trace_timed(None, 0, None, None, None, None, None, None, None, None) == 1
     # host path
     assert lib.pospopcnt_count_host(16, None, 4, good) == 1
     assert lib.pospopcnt_count_host(32, P((1 << 20) + 2), 4, good) == 2
