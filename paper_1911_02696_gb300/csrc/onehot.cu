@@ -232,6 +232,66 @@ __device__ __forceinline__ void encode_vec(uint32_t* d, const uint4& x, LutRef<I
   }
 }
 
+// Pairs of 8-bit ids below 16 (the bulk-copy kernel, k <= 16).  For a word
+// w of four such ids a, b, c, d (bytes 0..3), w + (w >> 4) -- one integer
+// multiply-add, mad.hi(w, 2^28, w), on the FMA pipe -- holds a | b << 4 in
+// byte 0 and c | d << 4 in byte 2 (no carries: every nibble sum is below
+// 256).  Row a | b << 4 of the pair table holds the encoded register of the
+// pair: one lookup for two ids, no combine.
+__device__ __forceinline__ uint32_t pack_id_pairs(uint32_t w) {
+  uint32_t d;
+  asm("mad.hi.u32 %0, %1, %2, %1;" : "=r"(d) : "r"(w), "r"(0x10000000u));
+  return d;
+}
+
+template <int LW>
+__device__ __forceinline__ uint32_t pair_lo(uint32_t row, uint32_t k) {
+  const uint32_t a = row & 15u, b = row >> 4;
+  const uint32_t ea = a < k ? 1u << a : 0u, eb = b < k ? 1u << b : 0u;
+  return LW == 16 ? ea | (eb << 16) : ea | (eb << 8);
+}
+
+template <int LW>
+__device__ __forceinline__ uint32_t pair_hi(uint32_t row, uint32_t k) {
+  return LW == 8 ? pair_lo<8>(row, k) << 16 : 0u;
+}
+
+template <int LW, uint32_t IMM>
+__device__ __forceinline__ void encode_vec_pairs(uint32_t* d, const uint4& x, LutRef<IMM> t, uint32_t lanebase,
+                                                 uint32_t one) {
+  const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const uint32_t pr = pack_id_pairs(w[q]);
+    const uint32_t off0 = __byte_perm(pr, lanebase, 0x7604u), off1 = __byte_perm(pr, lanebase, 0x7624u);
+    if constexpr (LW == 16) {
+      d[2 * q] = t.template at<0>(off0);
+      d[2 * q + 1] = t.template at<0>(off1);
+    } else {
+      d[q] = mad_one(t.template at<128>(off1), one, t.template at<0>(off0));
+    }
+  }
+}
+
+// Any 8-bit ids: clamped shift and mask per id (the trips that hold an id of
+// 16 or more, where the pair table does not apply).  km = (1 << k) - 1.
+template <int LW>
+__device__ __forceinline__ void encode_vec_shift(uint32_t* d, const uint4& x, uint32_t km) {
+  constexpr int IPR = 32 / LW;  // ids per register
+  const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+  for (int r = 0; r < 16 / IPR; ++r) {
+    uint32_t reg = 0;
+#pragma unroll
+    for (int q = 0; q < IPR; ++q) {
+      const int j = r * IPR + q;
+      const uint32_t id = __byte_perm(w[j / 4], 0u, 0x4440u | unsigned(j % 4));
+      reg |= shl_clamped(1u << (q * LW), id) & (km << (q * LW));
+    }
+    d[r] = reg;
+  }
+}
+
 // flush() with the additions on the FMA pipe.
 template <int K>
 __device__ __forceinline__ void flush_mad(uint32_t (&top)[K], uint32_t t, uint32_t one) {
@@ -444,6 +504,12 @@ struct RingCtl {
 };
 
 constexpr size_t RING_SMEM = size_t(LUT_BYTES) + size_t(RING_STAGES) * RING_CHUNK + sizeof(RingCtl);
+
+// The bulk-copy kernel's table is the pair table for 8-bit ids and k <= 16.
+template <int LW, int IDB>
+struct RingPairs {
+  static constexpr bool value = IDB == 1 && LW <= 16;
+};
 static_assert(RING_CHUNK % (16 * 4 * RING_CWARPS * 32) == 0 && RING_CHUNK % (16 * 2 * RING_CWARPS * 32) == 0,
               "a chunk is a whole number of consumer trips");
 constexpr uint64_t RING_MIN_BYTES = uint64_t(32) << 20;
@@ -452,16 +518,31 @@ constexpr uint64_t RING_MIN_BYTES = uint64_t(32) << 20;
 // lie past nv (the partial last chunk of the input) and read as ids 255.
 template <int LW, int IDB, uint32_t IMM, bool GUARD>
 __device__ __forceinline__ void ring_trip(const uint4* sv, uint32_t base, uint32_t nv, LutRef<IMM> t,
-                                          uint32_t lanebase, uint32_t one,
+                                          uint32_t lanebase, uint32_t one, uint32_t km,
                                           PairedCounts<LW, LutTrip<LW, IDB>::N>& acc) {
   constexpr int REGS_PER_VEC = LutTrip<LW, IDB>::REGS_PER_VEC, R = LutTrip<LW, IDB>::R, U = LutTrip<LW, IDB>::U;
   constexpr uint32_t CT = RING_CWARPS * 32;
-  uint32_t d[R];
+  uint4 y[U];
 #pragma unroll
   for (int j = 0; j < U; ++j) {
     const uint32_t idx = base + j * CT + threadIdx.x;
-    const uint4 y = (!GUARD || idx < nv) ? sv[idx] : make_uint4(~0u, ~0u, ~0u, ~0u);  // all-ones ids: nothing
-    encode_vec<LW, IDB, IMM>(d + j * REGS_PER_VEC, y, t, lanebase, one);
+    y[j] = (!GUARD || idx < nv) ? sv[idx] : make_uint4(~0u, ~0u, ~0u, ~0u);  // all-ones ids: nothing
+  }
+  uint32_t d[R];
+  if constexpr (RingPairs<LW, IDB>::value) {
+    uint32_t high = 0;  // any id of 16 or more in this thread's vectors
+#pragma unroll
+    for (int j = 0; j < U; ++j) high |= (y[j].x | y[j].y | y[j].z | y[j].w) & 0xF0F0F0F0u;
+    if (__all_sync(FULL_MASK, high == 0)) {
+#pragma unroll
+      for (int j = 0; j < U; ++j) encode_vec_pairs<LW, IMM>(d + j * REGS_PER_VEC, y[j], t, lanebase, one);
+    } else {
+#pragma unroll
+      for (int j = 0; j < U; ++j) encode_vec_shift<LW>(d + j * REGS_PER_VEC, y[j], km);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < U; ++j) encode_vec<LW, IDB, IMM>(d + j * REGS_PER_VEC, y[j], t, lanebase, one);
   }
   acc.add_trip(d, one);
 }
@@ -476,6 +557,7 @@ __device__ __forceinline__ uint32_t ring_consume(const OnehotArgs& a, const uint
   constexpr uint32_t TRIP = LutTrip<LW, IDB>::U * RING_CWARPS * 32;  // vectors per trip; divides a chunk
   constexpr uint32_t CV = RING_CHUNK / 16;                       // vectors per chunk
   const uint32_t one = a.one, lane = threadIdx.x & 31u;
+  const uint32_t km = a.k >= 32 ? ~0u : (1u << a.k) - 1u;
   // Only the input's last chunk can be partial; it is this CTA's last chunk
   // if this CTA holds it.
   const uint64_t body_bytes = a.nvec * 16;
@@ -497,10 +579,10 @@ __device__ __forceinline__ uint32_t ring_consume(const OnehotArgs& a, const uint
     if (i < full_chunks) {
 #pragma unroll
       for (uint32_t base = 0; base < CV; base += TRIP)
-        ring_trip<LW, IDB, IMM, false>(sv, base, CV, t, lanebase, one, acc);
+        ring_trip<LW, IDB, IMM, false>(sv, base, CV, t, lanebase, one, km, acc);
     } else {
       const uint32_t nv = uint32_t(body_bytes % RING_CHUNK) / 16u;
-      for (uint32_t base = 0; base < nv; base += TRIP) ring_trip<LW, IDB, IMM, true>(sv, base, nv, t, lanebase, one, acc);
+      for (uint32_t base = 0; base < nv; base += TRIP) ring_trip<LW, IDB, IMM, true>(sv, base, nv, t, lanebase, one, km, acc);
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&ctl->empty[s]);
@@ -535,8 +617,10 @@ __global__ void __launch_bounds__(RING_THREADS, 1) onehot_ring_kernel(OnehotArgs
     mbar_fence_init();
   }
   for (uint32_t e = warp; e < 256u; e += RING_CWARPS + 1) {
-    *reinterpret_cast<uint32_t*>(lut + e * LUT_ROW + lane * 4u) = lut_lo<LW>(e, a.k);
-    *reinterpret_cast<uint32_t*>(lut + e * LUT_ROW + 128u + lane * 4u) = lut_hi<LW>(e, a.k);
+    const bool pairs = RingPairs<LW, IDB>::value;
+    *reinterpret_cast<uint32_t*>(lut + e * LUT_ROW + lane * 4u) = pairs ? pair_lo<LW>(e, a.k) : lut_lo<LW>(e, a.k);
+    *reinterpret_cast<uint32_t*>(lut + e * LUT_ROW + 128u + lane * 4u) =
+        pairs ? pair_hi<LW>(e, a.k) : lut_hi<LW>(e, a.k);
   }
   __syncthreads();
 

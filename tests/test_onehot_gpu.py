@@ -87,6 +87,28 @@ def test_bulk_copy_sizes(idb, k):
     assert np.array_equal(_run(ids, k, idb), oracle.onehot_counts(ids, k))
 
 
+@pytest.mark.parametrize("k", [1, 3, 8, 9, 16])
+def test_u8_pairs_and_mixed_trips(k):
+    """8-bit ids all below 16 take the pair-table path of the bulk-copy
+    kernel (k <= 16), trips holding any id of 16 or more take the
+    shift-and-mask path: ids below k only, ids in [k, 16) (counted nowhere,
+    still the pair path), and the same input with a few ids >= 16 planted
+    at random places so that some trips switch path."""
+    rng = np.random.default_rng(300 + k)
+    n = (40 << 20) + 11
+    below_k = rng.integers(0, k, size=n).astype(np.uint8)
+    assert np.array_equal(_run(below_k, k, 3), oracle.onehot_counts(below_k, k))
+    below_16 = rng.integers(0, 16, size=n).astype(np.uint8)
+    assert np.array_equal(_run(below_16, k, 0), oracle.onehot_counts(below_16, k))
+    mixed = below_16.copy()
+    spots = rng.choice(n, size=200, replace=False)
+    mixed[spots] = rng.integers(16, 256, size=spots.size).astype(np.uint8)
+    mixed[spots[:50]] = 16  # the smallest id outside the pair table
+    got = _run(mixed, k, 5)
+    assert np.array_equal(got, oracle.onehot_counts(mixed, k))
+    assert int(got.sum()) == int(np.sum(mixed < k))
+
+
 @pytest.mark.parametrize("k", [1, 8, 16, 32])
 def test_u16_ids_with_high_bytes(k):
     """16-bit ids whose low byte is a valid category but whose high byte is
