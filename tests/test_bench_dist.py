@@ -65,3 +65,9 @@ def test_torchrun_reference_arm_prints_once():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+    # same workload and metric as the GPU arm's default line
+    sys.path.insert(0, ROOT)
+    import bench
+    _, width, _, desc = bench.make_input("u16", seed=0, limit=16)
+    assert d["config"]["workload"] == desc and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["higher_is_better"] is True
