@@ -169,7 +169,7 @@ int pospopcnt_batched(const void* d_in, const int64_t* d_offsets, size_t nseg, i
 /* Launch parameters of the batched form, per device and width.  unit_bytes:
  * the scheduling unit the warps claim from the work queue (4 KiB .. 1 MiB, a
  * multiple of 128); blocks_per_sm: CTAs per SM of the persistent grid (0: as
- * many as fit; more than fit is clamped).  Defaults: 16 KiB, 0.  The
+ * many as fit; more than fit is clamped).  Defaults: 32 KiB, 2.  The
  * paper's method has no such parameters; they tune the launch of the
  * segmented form (§5 notes that fixed costs dominate small inputs, which
  * these trade against load balance). */

@@ -25,11 +25,12 @@ DeviceState g_state[MAX_DEVICES];
 std::unordered_map<cudaStream_t, int> g_slots[MAX_DEVICES];
 pospopcnt_config g_cfg[MAX_DEVICES][4][NCLASSES];
 bool g_cfg_ready[MAX_DEVICES] = {};
-// Batched form, per device and width (8, 16, 32): 16 KiB units, as many
-// CTAs per SM as fit, until pospopcnt_batched_set_config/autotune.
+// Batched form, per device and width (8, 16, 32): 32 KiB units, 2 CTAs per
+// SM (what the autotuner picks on GB300 for the 20,000-segment log-uniform
+// layout), until pospopcnt_batched_set_config/autotune.
 pospopcnt_batched_config g_bcfg[MAX_DEVICES][3] = {};
 bool g_bcfg_set[MAX_DEVICES][3] = {};
-constexpr pospopcnt_batched_config BATCHED_DEFAULT = {16384, 0};
+constexpr pospopcnt_batched_config BATCHED_DEFAULT = {32768, 2};
 std::mutex g_host_mutex[MAX_DEVICES];
 std::atomic<uint64_t> g_launches{0};
 thread_local int t_last_cuda = 0;

@@ -28,7 +28,7 @@ struct bt_min_blocks {
 constexpr int BT_VPL = 8;
 template <int K>
 struct bt_batched_min_blocks {
-  static constexpr int value = K == 32 ? 3 : 4;
+  static constexpr int value = K == 32 ? 2 : 3;
 };
 
 // Pops the next tile index for the CTA (every thread gets it).

@@ -220,4 +220,4 @@ def test_batched_autotune_and_config():
                 ppc.pospopcnt_batched_set_config(16, bad)
     finally:
         ppc.pospopcnt_batched_set_config(16, None)
-    assert ppc.pospopcnt_batched_get_config(16) == {"unit_bytes": 16384, "blocks_per_sm": 0}
+    assert ppc.pospopcnt_batched_get_config(16) == {"unit_bytes": 32768, "blocks_per_sm": 2}
