@@ -61,7 +61,8 @@ def _run(server, dev, tr):
 def test_same_alone_and_in_the_mix(pool):
     host, dev = pool
     tr = _trace(1, rate=20000, duration=0.15, max_bytes=4 << 20)
-    srv = ppc.pospopcnt_server_create(0, max_inflight=8, max_batch_jobs=240)
+    # two slots: jobs that arrive while both are busy must share a launch
+    srv = ppc.pospopcnt_server_create(0, max_inflight=2, max_batch_jobs=240)
     try:
         lat, mixed, status = _run(srv, dev, tr)
         st = ppc.pospopcnt_server_get_stats(srv)
