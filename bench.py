@@ -191,24 +191,25 @@ def whole_job_throughput(bytes_per_rank_step: int, steps: int, world: int, max_m
 # ---------------------------------------------------------------------------
 # workloads
 
-def make_input(kind: str, seed: int, log2_words: int | None = None, limit: int | None = None):
+def make_input(kind: str, seed: int, log2_words: int | None = None, limit: int | None = None, onehot_k: int = 16):
     """(host words, width, start offset in bytes, description).  With `limit`
     only the first `limit` words are made -- the same words as the first ones
     of the full input, every generator being a function of (seed, index) --
     while the description still names the full workload."""
     import synth
-    zipf16 = synth.zipf_cdf(16)
+    K = int(onehot_k)
+    zipf16 = synth.zipf_cdf(K)  # the one-hot workloads' category distribution (k = 16 by default)
     if log2_words is not None:  # a smaller case of the same workload (profiling)
         n = 1 << log2_words
         table = {
             "popcount": (1, f"array popcount of 2^{log2_words} uniform random bytes",
                          lambda m: synth.uniform_bytes(seed, m)),
-            "onehot": (-16, f"fused one-hot encode + count: 2^{log2_words} u8 ids, Zipf(1.1) over 16 categories",
+            "onehot": (-K, f"fused one-hot encode + count: 2^{log2_words} u8 ids, Zipf(1.1) over {K} categories",
                        lambda m: synth.categorical_ids(seed, m, zipf16, np.uint8)),
-            "onehot_u16ids": (-16, f"fused one-hot encode + count: 2^{log2_words} u16 ids, Zipf(1.1) over 16 "
-                                   "categories", lambda m: synth.categorical_ids(seed, m, zipf16, np.uint16)),
-            "onehot_u32ids": (-16, f"fused one-hot encode + count: 2^{log2_words} u32 ids, Zipf(1.1) over 16 "
-                                   "categories", lambda m: synth.categorical_ids(seed, m, zipf16, np.uint32)),
+            "onehot_u16ids": (-K, f"fused one-hot encode + count: 2^{log2_words} u16 ids, Zipf(1.1) over {K} "
+                                  "categories", lambda m: synth.categorical_ids(seed, m, zipf16, np.uint16)),
+            "onehot_u32ids": (-K, f"fused one-hot encode + count: 2^{log2_words} u32 ids, Zipf(1.1) over {K} "
+                                  "categories", lambda m: synth.categorical_ids(seed, m, zipf16, np.uint32)),
         }
         width = {"u8": 8, "u32": 32, "u64": 64}.get(kind, 16)
         width, desc, gen = table.get(kind, (width, f"pospopcnt_u{width} n=2^{log2_words} uniform random bits",
@@ -226,13 +227,13 @@ def make_input(kind: str, seed: int, log2_words: int | None = None, limit: int |
                            lambda m: synth.uniform_bits(seed, m, 16)),
         "u8": (1 << 31, 8, 0, "pospopcnt_u8 n=2^31 uniform random bits (2 GiB)",
                lambda m: synth.uniform_bits(seed, m, 8)),
-        "onehot": (1 << 31, -16, 0, "fused one-hot encode + count: 2^31 u8 ids, Zipf(1.1) over 16 categories (2 GiB)",
+        "onehot": (1 << 31, -K, 0, f"fused one-hot encode + count: 2^31 u8 ids, Zipf(1.1) over {K} categories (2 GiB)",
                    lambda m: synth.categorical_ids(seed, m, zipf16, np.uint8)),
-        "onehot_u16ids": (1 << 30, -16, 0,
-                          "fused one-hot encode + count: 2^30 u16 ids, Zipf(1.1) over 16 categories (2 GiB)",
+        "onehot_u16ids": (1 << 30, -K, 0,
+                          f"fused one-hot encode + count: 2^30 u16 ids, Zipf(1.1) over {K} categories (2 GiB)",
                           lambda m: synth.categorical_ids(seed, m, zipf16, np.uint16)),
-        "onehot_u32ids": (1 << 29, -16, 0,
-                          "fused one-hot encode + count: 2^29 u32 ids, Zipf(1.1) over 16 categories (2 GiB)",
+        "onehot_u32ids": (1 << 29, -K, 0,
+                          f"fused one-hot encode + count: 2^29 u32 ids, Zipf(1.1) over {K} categories (2 GiB)",
                           lambda m: synth.categorical_ids(seed, m, zipf16, np.uint32)),
         "popcount": (1 << 31, 1, 0, "array popcount of 2 GiB of uniform random bits",
                      lambda m: synth.uniform_bytes(seed, m)),
@@ -306,7 +307,8 @@ def run_plain(args, world, rank, local):
     import paper_1911_02696_gb300 as ppc
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    words, width, offset, desc = make_input(args.workload, seed=rank, log2_words=args.log2_words)
+    words, width, offset, desc = make_input(args.workload, seed=rank, log2_words=args.log2_words,
+                                            onehot_k=args.onehot_k)
     nbytes = words.nbytes  # width 1 is the array popcount over bytes
     host = torch.from_numpy(words.view(np.uint8))
     buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
@@ -410,7 +412,7 @@ def run_plain(args, world, rank, local):
             "ms_per_step": round(max_ms / args.steps, 5),
             "ms_per_step_median": round(statistics.median(per_step), 5), "ms_per_step_min": round(min(per_step), 5),
             "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u8" if width == 1 else f"u{width}",
+            "vs_baseline": None, "dtype": f"u{8 * words.itemsize}" if onehot_k else "u8" if width == 1 else f"u{width}",
             "data": "synthetic (seeded SplitMix64 on the host)",
             "config": {"workload": desc, "n_words": int(words.size), "width": width, "start_offset_bytes": offset,
                        "bytes_per_rank_step": nbytes, "launch_config": cfg, "parallelism": f"replicas x{world}",
@@ -946,7 +948,8 @@ def run_reference(args, world, rank):
         return None
     import oracle
     kind = args.workload if args.workload in REFERENCE_WORKLOADS else "u16"
-    words, width, offset, desc = make_input(kind, seed=0, log2_words=args.log2_words, limit=1 << 26)
+    words, width, offset, desc = make_input(kind, seed=0, log2_words=args.log2_words, limit=1 << 26,
+                                            onehot_k=args.onehot_k)
     onehot_k = -width if width < 0 else 0
     cores = os.cpu_count() or 1
 
@@ -974,7 +977,7 @@ def run_reference(args, world, rank):
     return {"impl": "reference", "metric": metric,
             "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(dt * 1e3 / args.steps, 3), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u8" if width in (1, -16) else f"u{width}",
+            "vs_baseline": None, "dtype": f"u{8 * words.itemsize}" if width < 0 else "u8" if width == 1 else f"u{width}",
             "data": "synthetic (seeded SplitMix64 on the host)",
             "config": {"workload": desc, "width": 1 if onehot_k else width, "start_offset_bytes": offset,
                        "parallelism": "replicas x1", "sample_per_step": sample},
@@ -995,6 +998,8 @@ def main(argv=None):
                             "onehot_u16ids", "onehot_u32ids", "sweep", "batched",
                             "kernels", "autotune", "serve", "e2e", "peaks", "latency_floor", "l2_states"])
     p.add_argument("--batched-nseg", type=int, default=20000)
+    p.add_argument("--onehot-k", type=int, default=16, choices=range(1, 33), metavar="K",
+                   help="one-hot workloads: number of categories (1..32)")
     p.add_argument("--batched-autotune", action="store_true",
                    help="batched workload: autotune the launch on the layout before timing")
     p.add_argument("--serve-rate", type=float, default=50000.0)
