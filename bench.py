@@ -211,7 +211,7 @@ def make_input(kind: str, seed: int, log2_words: int | None = None, limit: int |
             "onehot_u32ids": (-K, f"fused one-hot encode + count: 2^{log2_words} u32 ids, Zipf(1.1) over {K} "
                                   "categories", lambda m: synth.categorical_ids(seed, m, zipf16, np.uint32)),
         }
-        width = {"u8": 8, "u32": 32, "u64": 64}.get(kind, 16)
+        width = {"u8": 8, "u8_onehot": 8, "u32": 32, "u32_onehot": 32, "u64": 64}.get(kind, 16)
         width, desc, gen = table.get(kind, (width, f"pospopcnt_u{width} n=2^{log2_words} uniform random bits",
                                             lambda m: synth.uniform_bits(seed, m, width)))
         return gen(min(n, limit or n)), width, 0, desc
@@ -227,6 +227,10 @@ def make_input(kind: str, seed: int, log2_words: int | None = None, limit: int |
                            lambda m: synth.uniform_bits(seed, m, 16)),
         "u8": (1 << 31, 8, 0, "pospopcnt_u8 n=2^31 uniform random bits (2 GiB)",
                lambda m: synth.uniform_bits(seed, m, 8)),
+        "u8_onehot": (1 << 31, 8, 0, "pospopcnt_u8 n=2^31 one-hot, position uniform over 8 (2 GiB)",
+                      lambda m: synth.one_hot(seed, m, 8, cdf=synth.uniform_cdf(8))),
+        "u32_onehot": (1 << 29, 32, 0, "pospopcnt_u32 n=2^29 one-hot, position uniform over 32 (2 GiB)",
+                       lambda m: synth.one_hot(seed, m, 32, cdf=synth.uniform_cdf(32))),
         "onehot": (1 << 31, -K, 0, f"fused one-hot encode + count: 2^31 u8 ids, Zipf(1.1) over {K} categories (2 GiB)",
                    lambda m: synth.categorical_ids(seed, m, zipf16, np.uint8)),
         "onehot_u16ids": (1 << 30, -K, 0,
@@ -936,7 +940,8 @@ def run_e2e(args, world, rank, local):
             "frac_of_link": round(res["pinned_in_place_GBps"] / res["memcpy_pinned_GBps"], 4)}
 
 
-REFERENCE_WORKLOADS = ("u16", "u16_onehot", "u16_sparse", "u16_misaligned", "u8", "u32", "u64", "popcount", "onehot",
+REFERENCE_WORKLOADS = ("u16", "u16_onehot", "u16_sparse", "u16_misaligned", "u8", "u8_onehot", "u32", "u32_onehot",
+                       "u64", "popcount", "onehot",
                        "onehot_u16ids", "onehot_u32ids")
 
 
@@ -994,7 +999,8 @@ def main(argv=None):
     p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="u16",
-                   choices=["u16", "u16_onehot", "u16_sparse", "u16_misaligned", "u8", "u32", "u64", "popcount", "onehot",
+                   choices=["u16", "u16_onehot", "u16_sparse", "u16_misaligned", "u8", "u8_onehot", "u32", "u32_onehot",
+                            "u64", "popcount", "onehot",
                             "onehot_u16ids", "onehot_u32ids", "sweep", "batched",
                             "kernels", "autotune", "serve", "e2e", "peaks", "latency_floor", "l2_states"])
     p.add_argument("--batched-nseg", type=int, default=20000)
