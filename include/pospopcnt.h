@@ -169,13 +169,15 @@ int pospopcnt_batched(const void* d_in, const int64_t* d_offsets, size_t nseg, i
 /* Launch parameters of the batched form, per device and width.  unit_bytes:
  * the scheduling unit the warps claim from the work queue (4 KiB .. 1 MiB, a
  * multiple of 128); blocks_per_sm: CTAs per SM of the persistent grid (0: as
- * many as fit; more than fit is clamped).  Defaults: 32 KiB, 2.  The
- * paper's method has no such parameters; they tune the launch of the
+ * many as fit; more than fit is clamped); ring_stages: depth of each warp's
+ * bulk-copy ring, 2, 3 or 4 stages of 4 KiB (0: 2).  Defaults: 32 KiB, 2, 2.
+ * The paper's method has no such parameters; they tune the launch of the
  * segmented form (§5 notes that fixed costs dominate small inputs, which
  * these trade against load balance). */
 typedef struct {
   int unit_bytes;
   int blocks_per_sm;
+  int ring_stages;
 } pospopcnt_batched_config;
 
 /* The configuration pospopcnt_batched (and its checked and graph forms)
@@ -185,7 +187,7 @@ int pospopcnt_batched_get_config(int width, pospopcnt_batched_config* cfg);
  * default).  POSPOPCNT_ERR_INVALID for an out-of-range field. */
 int pospopcnt_batched_set_config(int width, const pospopcnt_batched_config* cfg);
 /* Times every unit size in {4, 8, 16, 32, 64} KiB x CTAs per SM in {1, 2,
- * as many as fit} on the caller's own layout (warm-up + 5 timed calls each,
+ * as many as fit} x ring depth in {2, 3, 4} on the caller's own layout (warm-up + 5 timed calls each,
  * on `stream`, synchronous), checks that all of them produce identical rows
  * (POSPOPCNT_ERR_INVALID and nothing installed if not), installs the fastest
  * for `width` on the current device and returns it (and its mean time per

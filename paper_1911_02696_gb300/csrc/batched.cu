@@ -39,28 +39,29 @@ struct BatchedArgs {
 };
 
 // Per-warp bulk-copy ring: lane 0 streams the 16-byte-aligned body of a long
-// piece into RING_STAGES shared-memory stages of one trip (32 lanes x 8
+// piece into STAGES shared-memory stages of one trip (32 lanes x 8
 // vectors) each, one mbarrier per stage; the warp counts from shared memory
 // while the next trips are in flight.  Two stages of 4 KiB (64 KiB per CTA)
 // measured faster than three (96 KiB) on the 20,000-segment layout, and
 // faster than three stages of 2 KiB at any CTA count per SM.
-constexpr int RING_STAGES = 2;
+constexpr int RING_STAGES = 2;  // default ring depth (a launch may pick 3 or 4)
 constexpr int RING_VPL = 8;
 constexpr int TRIP_VECS = 32 * RING_VPL;
 constexpr int TRIP_BYTES = TRIP_VECS * 16;
 constexpr int RING_MIN_VECS = 2 * TRIP_VECS;  // shorter bodies are loaded directly
-constexpr size_t BT_RING_SMEM = size_t(BT_WARPS) * RING_STAGES * TRIP_BYTES;
+template <int STAGES>
+constexpr size_t bt_ring_smem() { return size_t(BT_WARPS) * STAGES * TRIP_BYTES; }
 
 struct WarpRing {
-  uint8_t* buf;    // RING_STAGES x TRIP_BYTES
-  uint64_t* full;  // RING_STAGES barriers
+  uint8_t* buf;    // STAGES x TRIP_BYTES
+  uint64_t* full;  // STAGES barriers
   uint32_t seq;    // trips issued (and consumed) by this warp so far
 };
 
 // warp_piece_counts with the body streamed through the warp's ring when it
 // is long enough.  Returns false (after recording the error) if a bounded
 // wait gave up; the warp then stops counting.
-template <int K>
+template <int K, int STAGES>
 __device__ __forceinline__ bool warp_piece_counts_ring(const uint8_t* base, uint64_t pa, uint64_t pb,
                                                        WarpRing& r, unsigned* err, uint32_t& out) {
   constexpr int WB = K / 8;
@@ -89,7 +90,7 @@ __device__ __forceinline__ bool warp_piece_counts_ring(const uint8_t* base, uint
   const uint4* src = reinterpret_cast<const uint4*>(bodyA);
   const uint32_t ntrips = uint32_t((nvec + TRIP_VECS - 1) / TRIP_VECS);
   auto issue = [&](uint32_t t) {  // lane 0 only
-    const uint32_t s = (r.seq + t) % RING_STAGES;
+    const uint32_t s = (r.seq + t) % STAGES;
     const uint64_t left = nvec - uint64_t(t) * TRIP_VECS;
     const uint32_t bytes = uint32_t(left < TRIP_VECS ? left : TRIP_VECS) * 16u;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier reads of the stage first
@@ -97,7 +98,7 @@ __device__ __forceinline__ bool warp_piece_counts_ring(const uint8_t* base, uint
     bulk_g2s(r.buf + size_t(s) * TRIP_BYTES, src + uint64_t(t) * TRIP_VECS, bytes, &r.full[s]);
   };
   if (lane == 0)
-    for (uint32_t t = 0; t < ntrips && t < uint32_t(RING_STAGES); ++t) issue(t);
+    for (uint32_t t = 0; t < ntrips && t < uint32_t(STAGES); ++t) issue(t);
 
   uint32_t B[L];
 #pragma unroll
@@ -107,14 +108,14 @@ __device__ __forceinline__ bool warp_piece_counts_ring(const uint8_t* base, uint
   for (int p = 0; p < K; ++p) top[p] = 0;
   for (uint32_t t = 0; t < ntrips; ++t) {
     const uint32_t seq = r.seq + t;
-    const uint32_t s = seq % RING_STAGES;
-    const bool ok = __all_sync(FULL_MASK, mbar_wait_bounded(&r.full[s], (seq / RING_STAGES) & 1u, WAIT_LIMIT_NS));
+    const uint32_t s = seq % STAGES;
+    const bool ok = __all_sync(FULL_MASK, mbar_wait_bounded(&r.full[s], (seq / STAGES) & 1u, WAIT_LIMIT_NS));
     if (!ok) {
       if (lane == 0) {
         atomicOr(err, ERR_BIT_TIMEOUT_FULL);
         // wait (bounded) for the copies still in flight into this warp's ring
-        for (uint32_t u = t; u < ntrips && u < t + RING_STAGES; ++u)
-          if (!mbar_wait_bounded(&r.full[(r.seq + u) % RING_STAGES], ((r.seq + u) / RING_STAGES) & 1u,
+        for (uint32_t u = t; u < ntrips && u < t + STAGES; ++u)
+          if (!mbar_wait_bounded(&r.full[(r.seq + u) % STAGES], ((r.seq + u) / STAGES) & 1u,
                                  WAIT_LIMIT_NS)) {
             atomicOr(err, ERR_BIT_TIMEOUT_DRAIN);
             break;
@@ -135,7 +136,7 @@ __device__ __forceinline__ bool warp_piece_counts_ring(const uint8_t* base, uint
     }
     flush<K>(top, Circuit<L>::run(d, B));
     __syncwarp();  // every lane has read the stage
-    if (lane == 0 && t + RING_STAGES < ntrips) issue(t + RING_STAGES);
+    if (lane == 0 && t + STAGES < ntrips) issue(t + STAGES);
   }
   r.seq += ntrips;
   uint32_t c[K];
@@ -148,31 +149,31 @@ __device__ __forceinline__ bool warp_piece_counts_ring(const uint8_t* base, uint
 
 // Counts words [pa, pb) of `base` with the whole warp and adds the result to
 // row[0..K-1]; false if a bounded wait gave up.
-template <int K>
+template <int K, int STAGES>
 __device__ __forceinline__ bool warp_count_piece(const uint8_t* base, uint64_t pa, uint64_t pb,
                                                  unsigned long long* row, WarpRing& ring, unsigned* err) {
   constexpr int SH = 5 - ilog2<K>::value;
   const int lane = threadIdx.x & 31;
   uint32_t v = 0;
-  if (!warp_piece_counts_ring<K>(base, pa, pb, ring, err, v)) return false;
+  if (!warp_piece_counts_ring<K, STAGES>(base, pa, pb, ring, err, v)) return false;
   if ((lane & ((1 << SH) - 1)) == 0 && v) atomicAdd(row + (lane >> SH), (unsigned long long)v);
   return true;
 }
 
-template <int K>
+template <int K, int STAGES>
 __global__ void __launch_bounds__(BT_THREADS, bt_batched_min_blocks<K>::value) batched_kernel(BatchedArgs a) {
   constexpr int WB = K / 8;
   extern __shared__ __align__(128) uint8_t bt_ring[];
-  __shared__ __align__(8) uint64_t bt_full[BT_WARPS][RING_STAGES];
+  __shared__ __align__(8) uint64_t bt_full[BT_WARPS][STAGES];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   if (*reinterpret_cast<volatile unsigned*>(&a.q->bad)) {  // the offsets check failed: touch no input
     retire_cta(a.q);
     return;
   }
-  WarpRing ring{bt_ring + size_t(warp) * RING_STAGES * TRIP_BYTES, bt_full[warp], 0};
+  WarpRing ring{bt_ring + size_t(warp) * STAGES * TRIP_BYTES, bt_full[warp], 0};
   if (lane == 0) {
-    for (int s = 0; s < RING_STAGES; ++s) mbar_init(&ring.full[s], 1);
+    for (int s = 0; s < STAGES; ++s) mbar_init(&ring.full[s], 1);
     mbar_fence_init();
   }
   __syncwarp();
@@ -227,7 +228,7 @@ __global__ void __launch_bounds__(BT_THREADS, bt_batched_min_blocks<K>::value) b
       const int64_t pa = seg_lo > w0 ? seg_lo : w0;
       const int64_t pb = seg_hi < w1 ? seg_hi : w1;
       if (pa < pb) {
-        if (!warp_count_piece<K>(a.base, uint64_t(pa), uint64_t(pb), a.counts + s * K, ring, a.err)) {
+        if (!warp_count_piece<K, STAGES>(a.base, uint64_t(pa), uint64_t(pb), a.counts + s * K, ring, a.err)) {
           failed = true;
           break;
         }
@@ -240,20 +241,31 @@ __global__ void __launch_bounds__(BT_THREADS, bt_batched_min_blocks<K>::value) b
   retire_cta(a.q);
 }
 
-template <int K>
-static int launch_batched_k(const DeviceState& st, const BatchedArgs& a, cudaStream_t stream,
+template <int K, int STAGES>
+static int launch_batched_ks(const DeviceState& st, const BatchedArgs& a, cudaStream_t stream,
                             int blocks_per_sm = 0) {
-  auto kern = batched_kernel<K>;
-  if (const cudaError_t e = ensure_dynamic_smem<batched_kernel<K>>(st.device, int(BT_RING_SMEM))) return cuda_fail(e);
+  auto kern = batched_kernel<K, STAGES>;
+  if (const cudaError_t e = ensure_dynamic_smem<batched_kernel<K, STAGES>>(st.device, int(bt_ring_smem<STAGES>()))) return cuda_fail(e);
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, BT_THREADS, BT_RING_SMEM) != cudaSuccess || occ < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, BT_THREADS, bt_ring_smem<STAGES>()) != cudaSuccess || occ < 1)
     occ = 1;
   const int bps = blocks_per_sm > 0 && blocks_per_sm < occ ? blocks_per_sm : occ;
   const unsigned grid = unsigned(st.sms) * unsigned(bps);
-  kern<<<grid, BT_THREADS, BT_RING_SMEM, stream>>>(a);
+  kern<<<grid, BT_THREADS, bt_ring_smem<STAGES>(), stream>>>(a);
   note_launch();
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? POSPOPCNT_OK : cuda_fail(e);
+}
+
+// ring_stages: the per-warp ring depth, 2 (default, also for 0), 3 or 4.
+template <int K>
+static int launch_batched_k(const DeviceState& st, const BatchedArgs& a, cudaStream_t stream, int blocks_per_sm = 0,
+                            int ring_stages = 0) {
+  switch (ring_stages) {
+    case 3: return launch_batched_ks<K, 3>(st, a, stream, blocks_per_sm);
+    case 4: return launch_batched_ks<K, 4>(st, a, stream, blocks_per_sm);
+    default: return launch_batched_ks<K, RING_STAGES>(st, a, stream, blocks_per_sm);
+  }
 }
 
 // Offsets check (checked batched form): offsets[0] >= 0, nondecreasing,
@@ -287,7 +299,7 @@ int launch_offsets_check(const DeviceState& st, const int64_t* d_offsets, size_t
 
 int launch_batched(const DeviceState& st, const void* d_in, const int64_t* d_offsets, size_t nseg,
                    int width, unsigned long long* d_counts, void* queue_slot, int tile_words,
-                   int blocks_per_sm, cudaStream_t stream) {
+                   int blocks_per_sm, int ring_stages, cudaStream_t stream) {
   BatchedArgs a;
   a.base = static_cast<const uint8_t*>(d_in);
   a.offsets = d_offsets;
@@ -297,9 +309,9 @@ int launch_batched(const DeviceState& st, const void* d_in, const int64_t* d_off
   a.tile_words = uint64_t(tile_words);
   a.err = st.d_err;
   switch (width) {
-    case 8: return launch_batched_k<8>(st, a, stream, blocks_per_sm);
-    case 16: return launch_batched_k<16>(st, a, stream, blocks_per_sm);
-    case 32: return launch_batched_k<32>(st, a, stream, blocks_per_sm);
+    case 8: return launch_batched_k<8>(st, a, stream, blocks_per_sm, ring_stages);
+    case 16: return launch_batched_k<16>(st, a, stream, blocks_per_sm, ring_stages);
+    case 32: return launch_batched_k<32>(st, a, stream, blocks_per_sm, ring_stages);
   }
   return POSPOPCNT_ERR_INVALID;
 }

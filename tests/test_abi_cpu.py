@@ -119,12 +119,13 @@ def test_argument_checks_need_no_device():
     assert lib.pospopcnt_batched(P((1 << 20) + 1), good, 3, 16, good, None) == 2
     assert lib.pospopcnt_batched(good, P((1 << 20) + 4), 3, 16, good, None) == 2
     # batched launch configuration: bad width, out-of-range fields, null outputs
-    cfg = ppc.BatchedConfig(16384, 0)
+    cfg = ppc.BatchedConfig(16384, 0, 0)
     assert lib.pospopcnt_batched_get_config(12, ctypes.byref(cfg)) == 1
     assert lib.pospopcnt_batched_get_config(16, None) == 1
-    for unit, bps in ((2048, 0), (4096 + 64, 0), (2 << 20, 0), (4096, -1), (4096, 33)):
-        bad = ppc.BatchedConfig(unit, bps)
-        assert lib.pospopcnt_batched_set_config(16, ctypes.byref(bad)) == 1, (unit, bps)
+    for unit, bps, stages in ((2048, 0, 0), (4096 + 64, 0, 0), (2 << 20, 0, 0), (4096, -1, 0), (4096, 33, 0),
+                              (4096, 0, 1), (4096, 0, 5)):
+        bad = ppc.BatchedConfig(unit, bps, stages)
+        assert lib.pospopcnt_batched_set_config(16, ctypes.byref(bad)) == 1, (unit, bps, stages)
     assert lib.pospopcnt_batched_set_config(64, None) == 1
     assert lib.pospopcnt_batched_autotune(good, good, 3, 16, good, None, None, None) == 1
     assert lib.pospopcnt_batched_autotune(good, good, 0, 16, good, ctypes.byref(cfg), None, None) == 1

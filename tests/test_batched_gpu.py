@@ -193,7 +193,7 @@ def test_native_graph_api():
 
 
 def test_batched_autotune_and_config():
-    """The autotuner times every unit size x CTAs-per-SM on the caller's
+    """The autotuner times every unit size x CTAs-per-SM x ring depth on the caller's
     layout, refuses to install unless all agree, and installs the fastest;
     counts stay bit-exact under every configuration, and out-of-range
     configurations are rejected."""
@@ -210,14 +210,16 @@ def test_batched_autotune_and_config():
         got = ppc.pospopcnt_batched(x, d_off, 16)
         assert np.array_equal(got.cpu().numpy().view(np.uint64), ref)
         for cfg in ({"unit_bytes": 4096, "blocks_per_sm": 1}, {"unit_bytes": 1 << 20, "blocks_per_sm": 32},
-                    {"unit_bytes": 8192 + 128, "blocks_per_sm": 0}):
+                    {"unit_bytes": 8192 + 128, "blocks_per_sm": 0}, {"unit_bytes": 16384, "ring_stages": 3},
+                    {"unit_bytes": 65536, "blocks_per_sm": 1, "ring_stages": 4}):
             ppc.pospopcnt_batched_set_config(16, cfg)
             got = ppc.pospopcnt_batched(x, d_off, 16)
             assert np.array_equal(got.cpu().numpy().view(np.uint64), ref), cfg
         for bad in ({"unit_bytes": 2048}, {"unit_bytes": 4096 + 64}, {"unit_bytes": 2 << 20},
-                    {"unit_bytes": 4096, "blocks_per_sm": -1}, {"unit_bytes": 4096, "blocks_per_sm": 33}):
+                    {"unit_bytes": 4096, "blocks_per_sm": -1}, {"unit_bytes": 4096, "blocks_per_sm": 33},
+                    {"unit_bytes": 4096, "ring_stages": 1}, {"unit_bytes": 4096, "ring_stages": 5}):
             with pytest.raises(ppc.PospopcntError):
                 ppc.pospopcnt_batched_set_config(16, bad)
     finally:
         ppc.pospopcnt_batched_set_config(16, None)
-    assert ppc.pospopcnt_batched_get_config(16) == {"unit_bytes": 32768, "blocks_per_sm": 2}
+    assert ppc.pospopcnt_batched_get_config(16) == {"unit_bytes": 32768, "blocks_per_sm": 2, "ring_stages": 2}
