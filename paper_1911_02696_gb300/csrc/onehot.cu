@@ -8,8 +8,11 @@
 // bits (the smallest that holds k positions), 32/LW ids share one 32-bit
 // register -- and feeds those registers through the same carry-save circuit
 // and popc flush as the plain count.  Ids >= k encode to the empty word.
-// 16- and 32-bit ids are encoded by a clamped shift and a mask (circuit F_4);
-// 8-bit ids by a lookup in shared memory (circuit F_5, or F_4 for 8-bit lanes).
+// 32-bit ids are encoded by a clamped shift and a mask (circuit F_4).  8- and
+// 16-bit ids are encoded by lookups in a table in shared memory
+// (onehot_lut_kernel below 32 MiB, onehot_ring_kernel from 32 MiB, the
+// latter fed by bulk copies); for 8-bit ids and k <= 16 the bulk-copy kernel
+// looks up pairs of ids below 16, one lookup for two ids.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -113,8 +116,8 @@ __global__ void __launch_bounds__(NTHREADS) onehot_kernel(OnehotArgs a) {
   block_reduce_add<LW, NTHREADS / 32>(c, a.counts, a.store != 0, int(k));
 }
 
-// 8-bit ids: the one-hot lane comes from a lookup table in shared memory
-// instead of a shift and a mask.  Row e of the table (256 bytes) holds, for
+// 8- and 16-bit ids: the one-hot lane comes from a lookup table in shared
+// memory instead of a shift and a mask.  Row e of the table (256 bytes) holds, for
 // each of the 32 lanes of a warp, its own copy of two encodings of id e: at
 // byte 4*l the low-lane word lo(e), at byte 128 + 4*l the high-lane word
 // hi(e) (both zero for e >= k).  The 32 lookups of a warp thus fall in 32
@@ -299,7 +302,7 @@ __device__ __forceinline__ void flush_mad(uint32_t (&top)[K], uint32_t t, uint32
   for (int p = 0; p < K; ++p) top[p] = mad_one(__popc(t & (lane_mask<K>::value << p)), one, top[p]);
 }
 
-// Per-thread counts of the 8-bit-id kernels.  A trip's circuit F_N returns
+// Per-thread counts of the lookup kernels.  A trip's circuit F_N returns
 // its top register (weight 2^N).  Top registers of consecutive trips are
 // combined as a binary counter of carry-save adders: two of weight 2^N give
 // a sum bit B[N] and a carry of weight 2^(N+1); two such carries give B[N+1]
