@@ -32,7 +32,7 @@ struct OnehotArgs {
   unsigned long long* counts;
   uint32_t k;
   uint32_t store;
-  uint32_t one;  // 1: multiplier of the FMA-pipe additions in the 8-bit-id kernels
+  uint32_t one;  // 1: multiplier of the FMA-pipe additions in the lookup kernels
   unsigned* err;  // device error word (bounded waits of the ring kernel)
 };
 
