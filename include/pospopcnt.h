@@ -258,9 +258,10 @@ int pospopcnt_plain_segments(const void* d_in, const int64_t* h_offsets, size_t 
  * that job complete as soon as its own last piece is counted, so a job never
  * waits for the rest of its batch.
  * Jobs of at least large_job_bytes are launched on their own with the
- * tuned plain count.  per_request = 1 launches every job that way (one
- * plain count per job), the comparison the batched form is measured
- * against. */
+ * tuned plain count (added into a row kept at zero, then published through
+ * the same flag by a one-warp kernel).  per_request = 1 launches every job
+ * that way (one plain count per job), the comparison the batched form is
+ * measured against. */
 typedef struct pospopcnt_server pospopcnt_server;
 
 typedef struct {
@@ -287,9 +288,10 @@ typedef struct {
   uint64_t bytes_completed, max_bytes_in_flight;
 } pospopcnt_server_stats;
 
-/* Creates a server on `device` (allocates its slots: per slot a stream, an
- * event, pinned descriptor and result buffers and device buffers) and starts
- * its worker thread.  cfg may be NULL for the defaults. */
+/* Creates a server on `device` (allocates its slots: per slot a stream,
+ * device rows and counters, and pinned mapped result and flag buffers that
+ * the GPU writes) and starts its worker thread.  cfg may be NULL for the
+ * defaults. */
 int pospopcnt_server_create(int device, const pospopcnt_server_config* cfg, pospopcnt_server** out);
 
 /* Waits for every submitted job, stops the worker and frees the server. */
