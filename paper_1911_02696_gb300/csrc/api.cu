@@ -69,7 +69,10 @@ pospopcnt_config tuned_default(int width, int cls) {
   pospopcnt_config c = default_config();
   if (width == 64) {  // two circuits per thread; the bulk-copy ring from 64 MiB
     if (cls >= 13) {
-      c.kernel = POSPOPCNT_KERNEL_TMA, c.stages = 3, c.chunk_bytes = 65536;
+      // 2 x 96 KiB: the autotuner's pick on GB300 at 256 MiB, 1 GiB and 2 GiB
+      // (with the evict-first hint from 256 MiB up)
+      c.kernel = POSPOPCNT_KERNEL_TMA, c.stages = 2, c.chunk_bytes = 98304;
+      if (cls >= 14) c.flags = POSPOPCNT_FLAG_EVICT_FIRST;
       return c;
     }
     c.threads = 256, c.unroll = cls <= 11 ? 4 : 8;
