@@ -356,9 +356,13 @@ int pospopcnt_get_config(int width, size_t n, pospopcnt_config* cfg);
 int pospopcnt_set_config(int width, int size_class, const pospopcnt_config* cfg);
 
 /* Times every candidate configuration on the caller's device buffer d_in
- * (n words) with CUDA events, installs the fastest for that width and size
- * class, and returns it in best (and its time in *best_ms).  d_scratch_counts:
- * device memory for width uint64 values.  Synchronous. */
+ * (n words) with CUDA events -- each candidate in three rounds interleaved
+ * with the others, each round about 2 ms of back-to-back calls (5 to 200),
+ * its median round kept -- checks that all candidates produce the same
+ * counts (POSPOPCNT_ERR_INVALID and nothing installed otherwise), installs
+ * the fastest for that width and size class, and returns it in best (and
+ * its time per call in *best_ms).  d_scratch_counts: device memory for width
+ * uint64 values.  Synchronous. */
 int pospopcnt_autotune(int width, const void* d_in, size_t n, uint64_t* d_scratch_counts,
                        pospopcnt_config* best, float* best_ms);
 
