@@ -187,11 +187,13 @@ int pospopcnt_batched_get_config(int width, pospopcnt_batched_config* cfg);
  * default).  POSPOPCNT_ERR_INVALID for an out-of-range field. */
 int pospopcnt_batched_set_config(int width, const pospopcnt_batched_config* cfg);
 /* Times every unit size in {4, 8, 16, 32, 64} KiB x CTAs per SM in {1, 2,
- * as many as fit} x ring depth in {2, 3, 4} on the caller's own layout (warm-up + 5 timed calls each,
- * on `stream`, synchronous), checks that all of them produce identical rows
- * (POSPOPCNT_ERR_INVALID and nothing installed if not), installs the fastest
- * for `width` on the current device and returns it (and its mean time per
- * call in ms if best_ms is not NULL).  d_counts receives the rows. */
+ * as many as fit} x ring depth in {2, 3, 4} on the caller's own layout (on
+ * `stream`, synchronous): three rounds interleaved across the candidates,
+ * about 2 ms of back-to-back calls per round, median round.  Checks that all
+ * of them produce identical rows (POSPOPCNT_ERR_INVALID and nothing
+ * installed if not), installs the fastest for `width` on the current device
+ * and returns it (and its time per call in ms if best_ms is not NULL).
+ * d_counts receives the rows. */
 int pospopcnt_batched_autotune(const void* d_in, const int64_t* d_offsets, size_t nseg, int width,
                                uint64_t* d_counts, pospopcnt_batched_config* best, float* best_ms,
                                cudaStream_t stream);

@@ -762,24 +762,29 @@ int pospopcnt_batched_autotune(const void* d_in, const int64_t* d_offsets, size_
     cudaEventDestroy(e0);
     return cuda_fail(e);
   }
-  float best_t = 1e30f;
-  int best_i = -1;
-  const int reps = 5;
+  // Times `reps` back-to-back calls of candidate i; mean ms per call.
+  auto time_calls = [&](size_t i, int reps, float* ms) -> int {
+    cudaEventRecord(e0, stream);
+    int r = POSPOPCNT_OK;
+    for (int k = 0; k < reps && r == POSPOPCNT_OK; ++k)
+      r = batched_impl(d_in, d_offsets, nseg, width, d_counts, stream, false, 0, &cands[i]);
+    cudaEventRecord(e1, stream);
+    if (r != POSPOPCNT_OK) return r;
+    const cudaError_t se = cudaEventSynchronize(e1);
+    if (se != cudaSuccess) return cuda_fail(se);
+    cudaEventElapsedTime(ms, e0, e1);
+    *ms /= float(reps);
+    return POSPOPCNT_OK;
+  };
+  // Pass 1: warm-up, a first timing (about 2 ms of calls per round
+  // afterwards, 3..200) and the check that every candidate agrees.
+  std::vector<int> reps(cands.size(), 3);
   for (size_t i = 0; i < cands.size() && rc == POSPOPCNT_OK; ++i) {
     rc = batched_impl(d_in, d_offsets, nseg, width, d_counts, stream, false, 0, &cands[i]);  // warm-up
-    if (rc != POSPOPCNT_OK) break;
-    cudaEventRecord(e0, stream);
-    for (int r = 0; r < reps && rc == POSPOPCNT_OK; ++r)
-      rc = batched_impl(d_in, d_offsets, nseg, width, d_counts, stream, false, 0, &cands[i]);
-    cudaEventRecord(e1, stream);
-    if (rc != POSPOPCNT_OK) break;
-    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
-      rc = cuda_fail(e);
-      break;
-    }
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    ms /= reps;
+    if (rc == POSPOPCNT_OK) rc = time_calls(i, 3, &ms);
+    if (rc != POSPOPCNT_OK) break;
+    reps[i] = std::max(3, std::min(200, int(2.0f / std::max(ms, 1e-4f))));
     if ((e = cudaMemcpy(got.data(), d_counts, sizeof(uint64_t) * row_words, cudaMemcpyDeviceToHost)) != cudaSuccess) {
       rc = cuda_fail(e);
       break;
@@ -790,11 +795,27 @@ int pospopcnt_batched_autotune(const void* d_in, const int64_t* d_offsets, size_
       rc = POSPOPCNT_ERR_INVALID;  // candidates disagree: refuse to tune
       break;
     }
-    if (ms < best_t) best_t = ms, best_i = int(i);
   }
+  // Three rounds, each timing every candidate once; median round.
+  constexpr int ROUNDS = 3;
+  std::vector<std::vector<float>> t(cands.size());
+  for (int round = 0; round < ROUNDS && rc == POSPOPCNT_OK; ++round)
+    for (size_t i = 0; i < cands.size() && rc == POSPOPCNT_OK; ++i) {
+      float ms = 0.f;
+      rc = time_calls(i, reps[i], &ms);
+      t[i].push_back(ms);
+    }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != POSPOPCNT_OK) return rc;
+  float best_t = 1e30f;
+  int best_i = -1;
+  for (size_t i = 0; i < cands.size(); ++i) {
+    std::vector<float> v = t[i];
+    std::sort(v.begin(), v.end());
+    const float med = v[v.size() / 2];
+    if (med < best_t) best_t = med, best_i = int(i);
+  }
   *best = cands[size_t(best_i)];
   if (best_ms) *best_ms = best_t;
   std::lock_guard<std::mutex> lk(g_mutex);
