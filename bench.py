@@ -687,6 +687,56 @@ def run_l2_states(args, world, rank, local):
             "rows": rows}
 
 
+def run_ring_ab(args, world, rank, local):
+    """Ring configurations of the bulk-copy kernel at 2 GiB, sustained: each
+    configuration counts the same buffer 1000 times back to back (CUDA events
+    around the 1000 calls, after 20 untimed ones), four rounds interleaved
+    across the configurations; GB/s per round and the median."""
+    import torch
+    import paper_1911_02696_gb300 as ppc
+    import synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ppc.pospopcnt_init(local)
+    stream = torch.cuda.current_stream(dev)
+    x = torch.from_numpy(synth.uniform_bytes(rank, 2 << 30)).to(dev)
+    cands = {
+        8: [dict(kernel="tma", stages=4, chunk_bytes=32768), dict(kernel="tma", stages=2, chunk_bytes=98304, flags=1),
+            dict(kernel="tma", stages=3, chunk_bytes=65536)],
+        16: [dict(kernel="tma", stages=4, chunk_bytes=49152), dict(kernel="tma", stages=3, chunk_bytes=65536),
+             dict(kernel="tma", stages=3, chunk_bytes=65536, flags=1), dict(kernel="tma", stages=2, chunk_bytes=98304)],
+        64: [dict(kernel="tma", stages=3, chunk_bytes=65536), dict(kernel="tma", stages=2, chunk_bytes=98304, flags=1),
+             dict(kernel="tma", stages=2, chunk_bytes=98304)],
+    }
+    rows = []
+    for width, cl in cands.items():
+        counts = torch.empty(width, dtype=torch.int64, device=dev)
+        res = [[] for _ in cl]
+        for _ in range(4):
+            for i, cfg in enumerate(cl):
+                for _ in range(20):
+                    ppc.pospopcnt_count_config(width, cfg, x, counts=counts)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                a.record(stream)
+                for _ in range(1000):
+                    ppc.pospopcnt_count_config(width, cfg, x, counts=counts)
+                b.record(stream)
+                torch.cuda.synchronize()
+                res[i].append(round(x.numel() * 1000 / (a.elapsed_time(b) * 1e-3) / 1e9, 1))
+        default = ppc.pospopcnt_get_config(width, x.numel() // (width // 8))
+        for i, cfg in enumerate(cl):
+            rows.append({"width": width, "config": cfg, "GBps_rounds": res[i],
+                         "median_GBps": statistics.median(res[i])})
+        rows.append({"width": width, "library_default": default})
+    if rank != 0:
+        return None
+    return {"metric": "pospopcnt GB/s by ring configuration (2 GiB, sustained)", "value": None, "unit": UNIT,
+            "n_gpus": world, "steps": 1000, "warmup": 20, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8/u16/u64", "data": "synthetic",
+            "config": {"workload": "2 GiB uniform bits, four interleaved rounds of 1000 calls"}, "rows": rows}
+
+
 def run_latency_floor(args, world, rank, local):
     """Launch-to-host latency floors of this GPU (the reference points of the
     serving path): builds and runs paper_1911_02696_gb300/latency_floor.cu."""
@@ -1002,7 +1052,8 @@ def main(argv=None):
                    choices=["u16", "u16_onehot", "u16_sparse", "u16_misaligned", "u8", "u8_onehot", "u32", "u32_onehot",
                             "u64", "popcount", "onehot",
                             "onehot_u16ids", "onehot_u32ids", "sweep", "batched",
-                            "kernels", "autotune", "serve", "e2e", "peaks", "latency_floor", "l2_states"])
+                            "kernels", "autotune", "serve", "e2e", "peaks", "latency_floor", "l2_states",
+                            "ring_ab"])
     p.add_argument("--batched-nseg", type=int, default=20000)
     p.add_argument("--onehot-k", type=int, default=16, choices=range(1, 33), metavar="K",
                    help="one-hot workloads: number of categories (1..32)")
@@ -1052,6 +1103,8 @@ def main(argv=None):
             out = run_latency_floor(args, world, rank, local)
         elif args.workload == "l2_states":
             out = run_l2_states(args, world, rank, local)
+        elif args.workload == "ring_ab":
+            out = run_ring_ab(args, world, rank, local)
         else:
             out = run_plain(args, world, rank, local)
         if world > 1:
