@@ -20,7 +20,8 @@
 //
 // Device side (serve_kernel): one CTA per 32 KiB tile of the batch's
 // virtual word space (short-lived CTAs, so batches on other streams share
-// the SMs at fine grain); each warp counts the pieces of its sub-range (segment helpers shared with the batched kernel) and adds them
+// the SMs at fine grain); each warp counts the pieces of its 4 KiB sub-range
+// in one trip (segment helpers shared with the batched kernel) and adds them
 // into the job's row in device memory.  Every warp then bumps the job's
 // piece counter; the warp that completes it (the number of sub-ranges a job
 // overlaps is known from its bounds) reads and re-zeroes the row, writes the
