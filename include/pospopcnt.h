@@ -198,6 +198,15 @@ int pospopcnt_batched_autotune(const void* d_in, const int64_t* d_offsets, size_
                                uint64_t* d_counts, pospopcnt_batched_config* best, float* best_ms,
                                cudaStream_t stream);
 
+/* Returns the work-queue slot that batched calls on `stream` hold on the
+ * current device (the library binds one of its 256 slots per device to
+ * each stream on that stream's first batched call).  Call it before
+ * destroying a stream that made batched calls, once none of its work is in
+ * flight; a later batched call on the stream binds a slot again.  OK if
+ * the stream holds none.  (pospopcnt_graph_destroy releases its graph's slot
+ * itself.)  Not in the paper: bookkeeping of the segmented form. */
+int pospopcnt_release_stream(cudaStream_t stream);
+
 /* A pospopcnt_batched call (its memset and its kernel) captured once into
  * an instantiated CUDA graph; each pospopcnt_graph_launch recounts the same
  * buffers (their contents may change between launches) with a single graph

@@ -139,6 +139,7 @@ def _declare(lib):
         "pospopcnt_batched_autotune": (i32, [vp, vp, sz, i32, vp, P(BatchedConfig), P(ctypes.c_float), vp]),
         "pospopcnt_graph_launch": (i32, [vp, vp]),
         "pospopcnt_graph_destroy": (i32, [vp]),
+        "pospopcnt_release_stream": (i32, [vp]),
         "pospopcnt_check_device_error": (i32, [vp]),
         "pospopcnt_plan_split": (i32, [i32, u64, sz, P(sz), P(sz), P(sz)]),
         "pospopcnt_get_config": (i32, [i32, sz, P(Config)]),
@@ -388,6 +389,15 @@ def pospopcnt_batched_autotune(x, offsets, width: int, counts=None, stream=None)
                                                  ctypes.byref(c), ctypes.byref(ms), _stream_handle(stream, x.device)),
                "pospopcnt_batched_autotune")
     return c.as_dict(), ms.value
+
+
+def pospopcnt_release_stream(stream=None, device=None) -> None:
+    """Returns the work-queue slot the stream's batched calls hold."""
+    torch = _torch()
+    dev = device if device is not None else torch.cuda.current_device()
+    with torch.cuda.device(dev):
+        _check(_lib().pospopcnt_release_stream(_stream_handle(stream, torch.device("cuda", dev))),
+               "pospopcnt_release_stream")
 
 
 def pospopcnt_batched_graph_create(x, offsets, width: int, counts) -> int:

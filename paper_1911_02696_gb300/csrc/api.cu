@@ -22,7 +22,12 @@ constexpr int NCLASSES = 21;  // floor(log4(bytes)) for bytes < 2^42
 
 std::mutex g_mutex;
 DeviceState g_state[MAX_DEVICES];
+// Work-queue slots of the batched form, per device: bound to a stream on its
+// first batched call, returned by pospopcnt_release_stream (or when a graph
+// that owns one is destroyed) and handed out again.
 std::unordered_map<cudaStream_t, int> g_slots[MAX_DEVICES];
+std::vector<int> g_free_slots[MAX_DEVICES];
+int g_next_slot[MAX_DEVICES] = {};
 pospopcnt_config g_cfg[MAX_DEVICES][4][NCLASSES];
 bool g_cfg_ready[MAX_DEVICES] = {};
 // Batched form, per device and width (8, 16, 32): 32 KiB units, 2 CTAs per
@@ -493,8 +498,14 @@ int batched_impl(const void* d_in, const int64_t* d_offsets, size_t nseg, int wi
     if (it != m.end()) {
       slot = it->second;
     } else {
-      if (int(m.size()) >= QUEUE_SLOTS) return POSPOPCNT_ERR_TOO_LARGE;
-      slot = int(m.size());
+      auto& fl = g_free_slots[st->device];
+      if (!fl.empty()) {
+        slot = fl.back();
+        fl.pop_back();
+      } else {
+        if (g_next_slot[st->device] >= QUEUE_SLOTS) return POSPOPCNT_ERR_TOO_LARGE;
+        slot = g_next_slot[st->device]++;
+      }
       m.emplace(stream, slot);
     }
   }
@@ -530,10 +541,25 @@ int pospopcnt_plain_segments(const void* d_in, const int64_t* h_offsets, size_t 
 
 }  // extern "C"
 
+namespace ppc {
+namespace {
+// Returns the work-queue slot bound to `stream` on `device` to the free list.
+void release_slot(int device, cudaStream_t stream) {
+  std::lock_guard<std::mutex> lk(g_mutex);
+  auto& m = g_slots[device];
+  auto it = m.find(stream);
+  if (it == m.end()) return;
+  g_free_slots[device].push_back(it->second);
+  m.erase(it);
+}
+}  // namespace
+}  // namespace ppc
+
 struct pospopcnt_graph {
   cudaStream_t stream = nullptr;  // the capture stream: its queue slot belongs to the graph
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  int device = -1;
 };
 
 extern "C" {
@@ -543,8 +569,10 @@ int pospopcnt_batched_graph_create(const void* d_in, const int64_t* d_offsets, s
   if (!out) return POSPOPCNT_ERR_INVALID;
   *out = nullptr;
   int rc = POSPOPCNT_OK;
-  if (!current_state(&rc)) return rc;  // workspace first: nothing is allocated during capture
+  DeviceState* st = current_state(&rc);  // workspace first: nothing is allocated during capture
+  if (!st) return rc;
   auto* g = new pospopcnt_graph();
+  g->device = st->device;
   cudaError_t e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) {
@@ -573,8 +601,19 @@ int pospopcnt_graph_destroy(pospopcnt_graph* g) {
   if (!g) return POSPOPCNT_ERR_INVALID;
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
-  if (g->stream) cudaStreamDestroy(g->stream);
+  if (g->stream) {
+    if (g->device >= 0) ppc::release_slot(g->device, g->stream);
+    cudaStreamDestroy(g->stream);
+  }
   delete g;
+  return POSPOPCNT_OK;
+}
+
+int pospopcnt_release_stream(cudaStream_t stream) {
+  int rc = POSPOPCNT_OK;
+  DeviceState* st = current_state(&rc);
+  if (!st) return rc;
+  ppc::release_slot(st->device, stream);
   return POSPOPCNT_OK;
 }
 

@@ -223,3 +223,26 @@ def test_batched_autotune_and_config():
     finally:
         ppc.pospopcnt_batched_set_config(16, None)
     assert ppc.pospopcnt_batched_get_config(16) == {"unit_bytes": 32768, "blocks_per_sm": 2, "ring_stages": 2}
+
+
+def test_stream_slots_are_released_and_reused():
+    """Each stream that makes batched calls holds one of 256 work-queue
+    slots; pospopcnt_release_stream returns it, so 300 short-lived streams
+    in turn never run out, and every count stays exact."""
+    rng = np.random.default_rng(11)
+    off = _layout(rng, 50, 3000, start=1)
+    words = synth.uniform_bits(11, int(off[-1]), 16)
+    _, x = _dev(words)
+    d_off = torch.from_numpy(off).cuda()
+    ref = oracle.pospopcnt_segments(words, off, 16)
+    for i in range(300):
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            out = ppc.pospopcnt_batched(x, d_off, 16, stream=s)
+        s.synchronize()
+        ppc.pospopcnt_release_stream(s)
+        if i % 50 == 0:
+            assert np.array_equal(out.cpu().numpy().view(np.uint64), ref), i
+        del s
+    ppc.pospopcnt_release_stream(torch.cuda.Stream())  # a stream without a slot: nothing to do
