@@ -1,8 +1,10 @@
 // Internal interfaces between the translation units of the library.
 #pragma once
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
 
 #include <cuda_runtime_api.h>
 
@@ -78,13 +80,18 @@ int launch_offsets_check(const DeviceState& st, const int64_t* d_offsets, size_t
 // kernel itself, not its type, which instances of one template share -- and
 // per device), so later launches, including launches captured into a CUDA
 // graph, make no attribute call.
+// Threads that race on the first launch take the mutex; the limit only
+// grows.
 template <auto Kern>
 cudaError_t ensure_dynamic_smem(int device, int bytes) {
-  static int done[64] = {};  // largest limit already set, per device
+  static std::atomic<int> done[64];  // largest limit already set, per device (zero-initialised)
+  static std::mutex mu;
   if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
-  if (done[device] >= bytes) return cudaSuccess;
+  if (done[device].load(std::memory_order_acquire) >= bytes) return cudaSuccess;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[device].load(std::memory_order_relaxed) >= bytes) return cudaSuccess;
   const cudaError_t e = cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess) done[device] = bytes;
+  if (e == cudaSuccess) done[device].store(bytes, std::memory_order_release);
   return e;
 }
 
