@@ -306,6 +306,7 @@ int check_args(int width, const void* d_in, size_t n, const void* d_counts) {
 }
 
 pospopcnt_config config_for(const DeviceState& st, int width, size_t n) {
+  std::lock_guard<std::mutex> lk(g_mutex);  // set_config / autotune may write the table concurrently
   return g_cfg[st.device][width_index(width)][size_class(uint64_t(n) * uint64_t(width / 8))];
 }
 
