@@ -351,6 +351,30 @@ struct PairedCounts {
   }
 };
 
+// The block's counts: each warp reduces its lanes' counters, warps
+// [0, CWARPS) leave their sums in `red` (CWARPS x LW words of shared memory
+// that no thread reads or writes any more), and threads 0..k-1 add them
+// into counts[p] with one atomic each, or store them when the grid is one
+// CTA.  Every thread of the block calls it.
+template <int LW, int CWARPS>
+__device__ __forceinline__ void reduce_counts_in(uint32_t* red, uint32_t (&c)[LW], const OnehotArgs& a) {
+  constexpr int SH = 5 - ilog2<LW>::value;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const uint32_t vsum = warp_reduce_positions<LW>(c);
+  __syncthreads();
+  if (warp < uint32_t(CWARPS) && (lane & ((1u << SH) - 1u)) == 0) red[warp * LW + (lane >> SH)] = vsum;
+  __syncthreads();
+  if (threadIdx.x < a.k) {
+    unsigned long long sum = 0;
+#pragma unroll
+    for (int w = 0; w < CWARPS; ++w) sum += red[w * LW + threadIdx.x];
+    if (a.store)
+      a.counts[threadIdx.x] = sum;
+    else if (sum)
+      atomicAdd(a.counts + threadIdx.x, sum);
+  }
+}
+
 // A trip is U = 4 vectors per thread (2 for one 8-bit id per register),
 // through the circuit F_N over their R = 2^N registers (N <= 5).
 template <int LW, int IDB>
@@ -442,23 +466,9 @@ __global__ void __launch_bounds__(NTHREADS, 3) onehot_lut_kernel(OnehotArgs a) {
       count_word<LW>(c, id < a.k ? 1u << id : 0u);
     }
   }
-  // Block reduction in the table's memory, which is free once every warp is
-  // past its last lookup; one atomic (or store) per position.
-  constexpr int NWARPS = NTHREADS / 32, SH = 5 - ilog2<LW>::value;
-  uint32_t* red = reinterpret_cast<uint32_t*>(lut);  // [NWARPS][LW]
-  const uint32_t vsum = warp_reduce_positions<LW>(c);
-  __syncthreads();
-  if ((lane & ((1u << SH) - 1u)) == 0) red[(threadIdx.x >> 5) * LW + (lane >> SH)] = vsum;
-  __syncthreads();
-  if (threadIdx.x < a.k) {
-    unsigned long long sum = 0;
-#pragma unroll
-    for (int w = 0; w < NWARPS; ++w) sum += red[w * LW + threadIdx.x];
-    if (a.store)
-      a.counts[threadIdx.x] = sum;
-    else if (sum)
-      atomicAdd(a.counts + threadIdx.x, sum);
-  }
+  // block reduction in the table's memory, free once every warp is past its
+  // last lookup
+  reduce_counts_in<LW, NTHREADS / 32>(reinterpret_cast<uint32_t*>(lut), c, a);
 }
 
 template <int LW, int IDB>
@@ -688,22 +698,8 @@ __global__ void __launch_bounds__(RING_THREADS, 1) onehot_ring_kernel(OnehotArgs
       count_word<LW>(c, id < a.k ? 1u << id : 0u);
     }
   }
-  // Block reduction in the table's memory (no lookup is left after the
-  // barrier above); the producer warp holds no counts.
-  constexpr int SH = 5 - ilog2<LW>::value;
-  uint32_t* red = reinterpret_cast<uint32_t*>(lut);  // [RING_CWARPS][LW]
-  const uint32_t vsum = warp_reduce_positions<LW>(c);
-  if (warp < RING_CWARPS && (lane & ((1u << SH) - 1u)) == 0) red[warp * LW + (lane >> SH)] = vsum;
-  __syncthreads();
-  if (threadIdx.x < a.k) {
-    unsigned long long sum = 0;
-#pragma unroll
-    for (int w = 0; w < RING_CWARPS; ++w) sum += red[w * LW + threadIdx.x];
-    if (a.store)
-      a.counts[threadIdx.x] = sum;
-    else if (sum)
-      atomicAdd(a.counts + threadIdx.x, sum);
-  }
+  // block reduction in the table's memory; the producer warp holds no counts
+  reduce_counts_in<LW, RING_CWARPS>(reinterpret_cast<uint32_t*>(lut), c, a);
 }
 
 template <int LW, int IDB>
