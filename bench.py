@@ -705,6 +705,8 @@ def run_ring_ab(args, world, rank, local):
             dict(kernel="tma", stages=3, chunk_bytes=65536)],
         16: [dict(kernel="tma", stages=4, chunk_bytes=49152), dict(kernel="tma", stages=3, chunk_bytes=65536),
              dict(kernel="tma", stages=3, chunk_bytes=65536, flags=1), dict(kernel="tma", stages=2, chunk_bytes=98304)],
+        32: [dict(kernel="tma", stages=3, chunk_bytes=65536), dict(kernel="tma", stages=4, chunk_bytes=49152),
+             dict(kernel="tma", stages=2, chunk_bytes=98304, flags=1), dict(kernel="tma", stages=4, chunk_bytes=32768)],
         64: [dict(kernel="tma", stages=3, chunk_bytes=65536), dict(kernel="tma", stages=2, chunk_bytes=98304, flags=1),
              dict(kernel="tma", stages=2, chunk_bytes=98304)],
     }
@@ -733,7 +735,7 @@ def run_ring_ab(args, world, rank, local):
         return None
     return {"metric": "pospopcnt GB/s by ring configuration (2 GiB, sustained)", "value": None, "unit": UNIT,
             "n_gpus": world, "steps": 1000, "warmup": 20, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u8/u16/u64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "u8/u16/u32/u64", "data": "synthetic",
             "config": {"workload": "2 GiB uniform bits, four interleaved rounds of 1000 calls"}, "rows": rows}
 
 
