@@ -306,6 +306,28 @@ def cpu_baseline(words, width, onehot_k=0, budget_s=8.0):
     return out
 
 
+def oracle_reference(words, width, onehot_k=0):
+    """The oracle's result for the whole input: its pospopcnt on all host
+    cores, or its one-hot and popcount routines over contiguous chunks on
+    host threads, the chunk results added (the definition is additive)."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    cores = os.cpu_count() or 1
+    if not onehot_k and width != 1:
+        return oracle.pospopcnt_mt(words, width, cores)[0]
+    chunk = max(1, -(-words.size // cores))
+    parts = [words[i: i + chunk] for i in range(0, words.size, chunk)]
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        if onehot_k:
+            res = list(ex.map(lambda part: oracle.onehot_counts(part, onehot_k), parts))
+            return np.sum(np.stack(res), axis=0, dtype=np.uint64) if res else np.zeros(onehot_k, np.uint64)
+        return np.array([sum(ex.map(oracle.popcount, parts))], dtype=np.uint64)
+
+
+class CheckFailed(RuntimeError):
+    """A timed result differs from the oracle's: the bench prints no value."""
+
+
 def run_plain(args, world, rank, local):
     import torch
     import paper_1911_02696_gb300 as ppc
@@ -338,8 +360,6 @@ def run_plain(args, world, rank, local):
           1: lambda t, counts: ppc.pospopcnt_popcount(t, count=counts)}[width]
     stream = torch.cuda.current_stream(dev)
 
-    # correctness of the timed configuration (oracle on rank 0's host copy is
-    # done by the tests; here a cheap invariant: the popcount total)
     fn(x, counts=counts)
     torch.cuda.synchronize()
 
@@ -363,6 +383,11 @@ def run_plain(args, world, rank, local):
     launches = ppc.pospopcnt_launch_count() - launches0
     time.sleep(0.3)
     clocks.stop()
+    # the counts of the last timed step against the oracle on the whole input
+    got = counts.cpu().numpy().view(np.uint64).copy()
+    ref = oracle_reference(words, width, onehot_k)
+    if not np.array_equal(got, ref):
+        raise CheckFailed(f"rank {rank}: timed counts {got.tolist()} differ from the oracle's {ref.tolist()}")
     total_ms = ev[0].elapsed_time(ev[-1])
     per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     max_ms = dist_max(total_ms, world, device=dev if world > 1 else None)
@@ -377,11 +402,41 @@ def run_plain(args, world, rank, local):
         dist_barrier(world)
         t0 = time.perf_counter()
         for _ in range(k_e2e):
-            ppc.pospopcnt_count_host(width, pinned)
+            got_e2e = ppc.pospopcnt_count_host(width, pinned)
         e2e_s = dist_max(time.perf_counter() - t0, world, device=dev if world > 1 else None)
+        if not np.array_equal(got_e2e, ref):
+            raise CheckFailed(f"rank {rank}: host-buffer counts differ from the oracle's")
         e2e = {"value": round(nbytes * k_e2e * world / e2e_s / 1e9, 3), "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": width * 8, "steps": k_e2e}
 
+    # the metric's other two numbers, on the default workload at one GPU:
+    # batched segments/s (20,000 segments, one graph-replayed launch vs 20,000
+    # plain launches) and served p50 / p99 (a short trace, both modes)
+    extras = None
+    if (world == 1 and not args.no_extras and args.workload == "u16" and args.log2_words is None
+            and not args.kernel):
+        del x, buf
+        torch.cuda.empty_cache()
+        b = measure_batched(local, rank, 20000, warmup=3, steps=min(args.steps, 20))
+        sv = measure_serve(local, rank, 50000.0, args.extras_serve_seconds, 16, 16)
+        bm, pm = sv["modes"]["batched"], sv["modes"]["per_request"]
+        extras = {
+            "batched_segments_per_s": round(b["segments_per_s"], 1),
+            "batched_GBps": round(b["GBps"], 1),
+            "batched_vs_plain": round(b["plain_ms"] / b["ms"], 2),
+            "serve_p50_us": round(bm["p50_ms"] * 1e3, 2), "serve_p99_us": round(bm["p99_ms"] * 1e3, 2),
+            "serve_per_request_p50_us": round(pm["p50_ms"] * 1e3, 2),
+            "serve_per_request_p99_us": round(pm["p99_ms"] * 1e3, 2),
+            "serve_p99_vs_per_request": round(pm["p99_ms"] / bm["p99_ms"], 3),
+            "extras_config": {
+                "batched": f"20,000 u16 segments log-uniform [1, 2^20] words ({b['total_bytes']} bytes), one-hot "
+                           f"rotated Zipf(1.1); one graph-replayed batched launch ({b['ms']:.4f} ms, mean of "
+                           f"{b['steps']}) vs 20,000 plain launches from the host loop ({b['plain_ms']:.3f} ms); "
+                           + b["checked"],
+                "serve": f"Poisson 50,000 req/s for {args.extras_serve_seconds:g} s ({sv['requests']} requests), "
+                         "widths 8/16/32, sizes log-uniform 1 KiB..256 MiB, budget 64 GiB, 16 slots in both "
+                         f"modes; mean jobs per batched launch {bm['mean_jobs_per_batch']}; " + sv["checked"]},
+        }
     peak, peak_src = peak_hbm()
     launch_ms = statistics.mean(per_step)
     counts_bytes = (onehot_k or width) * 8
@@ -430,7 +485,12 @@ def run_plain(args, world, rank, local):
             "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clocks.summary(),
+            "checked": True,
+            "checked_against": "oracle on the whole input (host threads), counts of the last timed step, "
+                               "bit-exact",
         }
+        if extras:
+            out.update(extras)
         if not args.no_cpu_baseline and world == 1:
             out["cpu_baseline"] = cpu_baseline(words, width, onehot_k)
     return out
@@ -502,17 +562,29 @@ def run_sweep(args, world, rank, local):
             "floors": floors, "points": points}
 
 
-def run_batched(args, world, rank, local):
-    """20,000 segments, lengths log-uniform in [1, 2^20] words, one-hot
-    rotated Zipf(1.1) per segment: one batched launch (replayed from a CUDA
-    graph) vs 20,000 plain pospopcnt_u16 launches on one stream."""
+def oracle_segments(words, off, width):
+    """The oracle's rows for every segment, computed over groups of
+    consecutive segments on host threads."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    nseg = off.size - 1
+    cores = os.cpu_count() or 1
+    bounds = np.linspace(0, nseg, min(nseg, 4 * cores) + 1).astype(np.int64)
+    groups = [(int(a), int(b)) for a, b in zip(bounds[:-1], bounds[1:]) if b > a]
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        rows = list(ex.map(lambda g: oracle.pospopcnt_segments(words, off[g[0]: g[1] + 1], width), groups))
+    return np.concatenate(rows, axis=0)
+
+
+def measure_batched(local, rank, nseg, warmup, steps, autotune=False):
+    """nseg segments, lengths log-uniform in [1, 2^20] words, one-hot rotated
+    Zipf(1.1) per segment: one batched launch replayed from a CUDA graph vs
+    nseg plain pospopcnt_u16 launches on one stream, both checked
+    bit-exactly against the oracle's rows."""
     import torch
     import paper_1911_02696_gb300 as ppc
     import synth
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    ppc.pospopcnt_init(local)
-    nseg = args.batched_nseg
     lens = synth.log_uniform_lengths(rank, nseg)
     off = synth.offsets_from_lengths(lens)
     words = synth.segmented_one_hot(rank, off, 16)
@@ -522,31 +594,34 @@ def run_batched(args, world, rank, local):
     s = torch.cuda.Stream(dev)
     s.wait_stream(torch.cuda.current_stream(dev))
     tuned = None
-    if args.batched_autotune:  # tune the launch on this layout first (installed for width 16)
+    if autotune:  # tune the launch on this layout first (installed for width 16)
         best, best_ms = ppc.pospopcnt_batched_autotune(x, d_off, 16, counts=out, stream=s)
         tuned = {"config": best, "autotune_ms_per_call": round(best_ms, 4)}
     with torch.cuda.stream(s):
-        for _ in range(max(args.warmup, 1)):
+        for _ in range(max(warmup, 1)):
             ppc.pospopcnt_batched(x, d_off, 16, counts=out, stream=s)
     s.synchronize()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=s):
         ppc.pospopcnt_batched(x, d_off, 16, counts=out, stream=s)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         g.replay()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    steps = max(1, min(args.steps, 50))
+    steps = max(1, min(steps, 50))
     cur = torch.cuda.current_stream(dev)
     torch.cuda.synchronize()
+    launches0 = ppc.pospopcnt_launch_count()
     a.record(cur)
     for _ in range(steps):
         g.replay()
     b.record(cur)
     torch.cuda.synchronize()
     batched_ms = a.elapsed_time(b) / steps
-    got = out.cpu().numpy().view(np.uint64)
-    assert np.array_equal(got.sum(axis=1), lens.astype(np.uint64)), "one-hot row sums"
-    # 20,000 plain launches on one stream, same data: from the native host
+    got = out.cpu().numpy().view(np.uint64).copy()
+    ref = oracle_segments(words, off, 16)
+    if not np.array_equal(got, ref):
+        raise CheckFailed(f"rank {rank}: batched rows differ from the oracle's")
+    # nseg plain launches on one stream, same data: from the native host
     # loop, and replayed from a CUDA graph that captured that loop
     plain_out = torch.empty((nseg, 16), dtype=torch.int64, device=dev)
     with torch.cuda.stream(s):
@@ -558,7 +633,8 @@ def run_batched(args, world, rank, local):
     b.record(s)
     torch.cuda.synchronize()
     plain_ms = a.elapsed_time(b)
-    assert np.array_equal(plain_out.cpu().numpy().view(np.uint64), got), "plain vs batched"
+    if not np.array_equal(plain_out.cpu().numpy().view(np.uint64), ref):
+        raise CheckFailed(f"rank {rank}: plain per-segment rows differ from the oracle's")
     g2 = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g2, stream=s):
         ppc.pospopcnt_plain_segments(x, off, 16, counts=plain_out, stream=s)
@@ -570,21 +646,41 @@ def run_batched(args, world, rank, local):
     torch.cuda.synchronize()
     plain_graph_ms = a.elapsed_time(b)
     total = int(off[-1]) * 2
+    del g, g2, x, d_off, out, plain_out
+    torch.cuda.empty_cache()
+    return {"segments": nseg, "total_bytes": total, "ms": batched_ms, "steps": steps,
+            "segments_per_s": nseg / (batched_ms * 1e-3), "GBps": total / (batched_ms * 1e-3) / 1e9,
+            "plain_ms": plain_ms, "plain_graph_ms": plain_graph_ms, "tuned": tuned,
+            "launch_config": ppc.pospopcnt_batched_get_config(16),
+            "checked": "batched and plain rows equal the oracle's, bit-exact"}
+
+
+def run_batched(args, world, rank, local):
+    """20,000 segments, lengths log-uniform in [1, 2^20] words, one-hot
+    rotated Zipf(1.1) per segment: one batched launch (replayed from a CUDA
+    graph) vs 20,000 plain pospopcnt_u16 launches on one stream."""
+    import torch
+    import paper_1911_02696_gb300 as ppc
+    torch.cuda.set_device(local)
+    ppc.pospopcnt_init(local)
+    m = measure_batched(local, rank, args.batched_nseg, args.warmup, args.steps, args.batched_autotune)
+    nseg = m["segments"]
     if rank != 0:
         return None
-    return {"metric": "batched segments/s", "value": round(nseg / (batched_ms * 1e-3), 1), "unit": "segments/s",
-            "n_gpus": world, "steps": steps, "warmup": args.warmup, "ms_per_step": round(batched_ms, 4),
+    return {"metric": "batched segments/s", "value": round(m["segments_per_s"], 1), "unit": "segments/s",
+            "n_gpus": world, "steps": m["steps"], "warmup": args.warmup, "ms_per_step": round(m["ms"], 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
-            "data": "synthetic", "config": {"workload": "20,000 segments log-uniform [1, 2^20] words, one-hot "
+            "data": "synthetic", "config": {"workload": f"{nseg:,} segments log-uniform [1, 2^20] words, one-hot "
                                                         "rotated Zipf(1.1), one graph-replayed batched launch",
-                                            "total_bytes": total,
-                                            "launch_config": ppc.pospopcnt_batched_get_config(16),
-                                            "autotuned": tuned},
-            "batched_GBps": round(total / (batched_ms * 1e-3) / 1e9, 1),
-            "plain_launches": {"ms": round(plain_ms, 3), "segments_per_s": round(nseg / (plain_ms * 1e-3), 1),
-                               "graph_ms": round(plain_graph_ms, 3),
-                               "graph_segments_per_s": round(nseg / (plain_graph_ms * 1e-3), 1)},
-            "speedup_vs_plain": round(plain_ms / batched_ms, 2)}
+                                            "total_bytes": m["total_bytes"],
+                                            "launch_config": m["launch_config"],
+                                            "autotuned": m["tuned"]},
+            "batched_GBps": round(m["GBps"], 1),
+            "plain_launches": {"ms": round(m["plain_ms"], 3),
+                               "segments_per_s": round(nseg / (m["plain_ms"] * 1e-3), 1),
+                               "graph_ms": round(m["plain_graph_ms"], 3),
+                               "graph_segments_per_s": round(nseg / (m["plain_graph_ms"] * 1e-3), 1)},
+            "speedup_vs_plain": round(m["plain_ms"] / m["ms"], 2), "checked": m["checked"]}
 
 
 def run_peaks(args, world, rank, local):
@@ -739,36 +835,6 @@ def run_ring_ab(args, world, rank, local):
             "config": {"workload": "2 GiB uniform bits, four interleaved rounds of 1000 calls"}, "rows": rows}
 
 
-def run_latency_floor(args, world, rank, local):
-    """Launch-to-host latency floors of this GPU (the reference points of the
-    serving path): builds and runs paper_1911_02696_gb300/latency_floor.cu."""
-    if rank != 0:
-        return None
-    src = os.path.join(ROOT, "paper_1911_02696_gb300", "latency_floor.cu")
-    out_dir = os.path.join(ROOT, "paper_1911_02696_gb300", "_build")
-    os.makedirs(out_dir, exist_ok=True)
-    exe = os.path.join(out_dir, "latency_floor")
-    subprocess.check_call(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-o", exe, src])
-    res = subprocess.run([exe], capture_output=True, text=True, timeout=300)
-    paths = {}
-    status = None
-    for line in res.stdout.splitlines():
-        parts = line.split("|")
-        if parts[0] == "status":
-            status = parts[1:]
-        elif len(parts) == 5:
-            paths[parts[0]] = {"p50_us": float(parts[1]), "p90_us": float(parts[2]), "p99_us": float(parts[3]),
-                               "min_us": float(parts[4])}
-    if res.returncode != 0 or not paths:
-        raise RuntimeError(f"latency_floor failed: rc={res.returncode} {res.stdout[-400:]} {res.stderr[-400:]}")
-    flag = paths["flag kernel, 16 B parameters, host spin"]
-    return {"metric": "launch to host-visible flag latency", "value": flag["p50_us"], "unit": "us",
-            "n_gpus": world, "steps": 2000, "warmup": 2000, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u32", "data": "none (latency probe)",
-            "config": {"workload": "one-block kernels, host timing from the launch call to the result seen"},
-            "paths": paths, "cuda_status": status}
-
-
 def candidate_configs():
     cfgs = [dict(kernel="csa", threads=t, unroll=u) for t in (128, 256, 512) for u in (2, 4, 8)]
     cfgs += [dict(kernel="tma", stages=st, chunk_bytes=c, flags=fl) for st in (2, 3, 4, 6, 8)
@@ -853,34 +919,40 @@ def run_autotune(args, world, rank, local):
             "table": table}
 
 
-def run_serve(args, world, rank, local):
-    """Serving: open-loop Poisson arrivals (50k req/s by default) of requests
-    with width 8/16/32 (weights 0.2/0.6/0.2) and payloads log-uniform in
-    1 KiB..256 MiB, each a slice of a 4 GiB device pool of uniform random
-    bits, HBM admission budget 64 GiB.  The same trace is served by the
-    continuous-batching runtime and by per-request plain launches; latency
-    = completion seen on the host - scheduled arrival."""
+def measure_serve(local, rank, rate, seconds, slots, slots_plain, large_mib=4.0, large_inflight=0,
+                  max_kib=256 * 1024, modes=("batched", "per_request"), oracle_sample=200, pool=None):
+    """Serving: open-loop Poisson arrivals at `rate` per second for `seconds`
+    of requests with width 8/16/32 (weights 0.2/0.6/0.2) and payloads
+    log-uniform in 1 KiB..max_kib KiB, each a slice of a 4 GiB device pool of
+    uniform random bits, HBM admission budget 64 GiB.  The same trace runs
+    through the continuous-batching runtime and through per-request plain
+    launches; latency = completion seen on the host - scheduled arrival.
+    Every request's counts must be equal in both modes (each job in
+    per-request mode is counted alone), and a sample of the small requests
+    equal to the oracle on a host copy of their payload."""
     import torch
+    import oracle
     import paper_1911_02696_gb300 as ppc
     import synth
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    ppc.pospopcnt_init(local)
     pool_bytes = 4 << 30
-    pool = torch.from_numpy(synth.uniform_bytes(100 + rank, pool_bytes)).to(dev)
-    tr = synth.serving_trace(rank, rate=args.serve_rate, duration=args.serve_seconds, pool_bytes=pool_bytes)
+    if pool is None:
+        pool = torch.from_numpy(synth.uniform_bytes(100 + rank, pool_bytes)).to(dev)
+    tr = synth.serving_trace(rank, rate=rate, duration=seconds, pool_bytes=pool_bytes,
+                             max_bytes=int(max_kib) * 1024)
     n = tr["t_arrival"].size
     wb = (tr["width"] // 8).astype(np.uint64)
     nbytes = tr["nwords"] * wb
     addr = np.uint64(pool.data_ptr()) + tr["offset_bytes"].astype(np.uint64)
     total = int(nbytes.sum())
+    large = nbytes >= int(large_mib * (1 << 20))
 
     def serve(per_request):
         srv = ppc.pospopcnt_server_create(local, hbm_budget_bytes=64 << 30, per_request=per_request,
-                                          max_inflight=args.serve_slots_plain if per_request else args.serve_slots,
+                                          max_inflight=slots_plain if per_request else slots,
                                           max_batch_jobs=1 if per_request else 240,
-                                          large_job_bytes=int(args.serve_large_mib * (1 << 20)),
-                                          max_large_inflight=0 if per_request else args.serve_large_inflight)
+                                          large_job_bytes=int(large_mib * (1 << 20)),
+                                          max_large_inflight=0 if per_request else large_inflight)
         try:
             # warm-up: a short slice of the trace
             k = min(n, 2000)
@@ -894,17 +966,16 @@ def run_serve(args, world, rank, local):
             st = ppc.pospopcnt_server_get_stats(srv)
         finally:
             ppc.pospopcnt_server_destroy(srv)
-        assert np.all(status == 0), "requests failed"
+        if not np.all(status == 0):
+            raise CheckFailed(f"rank {rank}: {int(np.sum(status != 0))} requests failed")
         q = np.percentile(lat, [50, 99, 99.9]) * 1e3
-        large = nbytes >= int(args.serve_large_mib * (1 << 20))
 
         def breakdown(mask):  # microseconds from arrival: p50 / p99 of each stage boundary
             if not mask.any():
                 return None
             st_us = stages[mask] * 1e6
-            names = ("admit", "launch", "done")
             out = {"requests": int(mask.sum())}
-            for k, nm in enumerate(names):
+            for k, nm in enumerate(("admit", "launch", "done")):
                 out[f"{nm}_p50_us"] = round(float(np.percentile(st_us[:, k], 50)), 2)
                 out[f"{nm}_p99_us"] = round(float(np.percentile(st_us[:, k], 99)), 2)
             gpu = st_us[:, 2] - st_us[:, 1]
@@ -914,40 +985,73 @@ def run_serve(args, world, rank, local):
         return {"p50_ms": round(float(q[0]), 4), "p99_ms": round(float(q[1]), 4), "p999_ms": round(float(q[2]), 4),
                 "max_ms": round(float(lat.max()) * 1e3, 4), "mean_ms": round(float(lat.mean()) * 1e3, 4),
                 "aggregate_GBps": round(total / wall / 1e9, 2), "wall_s": round(wall, 3),
+                "slots": slots_plain if per_request else slots,
                 "batches": st["batches"], "mean_jobs_per_batch": round(st["jobs_in_batches"] / max(st["batches"], 1), 2),
                 "max_batch": st["max_batch"], "deferrals": st["deferrals"],
                 "max_GiB_in_flight": round(st["max_bytes_in_flight"] / 2**30, 3),
                 "stages_small": breakdown(~large), "stages_large": breakdown(large)}, counts
 
-    batched, c_b = serve(False)
-    plain, c_p = serve(True)
-    # each result alone (its own plain call) vs in the mix, on a sample
-    rng = np.random.default_rng(0)
-    sample = rng.choice(n, size=min(n, 2000), replace=False)
-    solo = torch.zeros((sample.size, 32), dtype=torch.int64, device=dev)
-    for r, i in enumerate(sample):
-        w = int(tr["width"][i])
-        o = int(tr["offset_bytes"][i])
-        ppc.pospopcnt_count(w, pool[o:o + int(nbytes[i])], counts=solo[r, :w])
-    torch.cuda.synchronize()
-    solo_np = solo.cpu().numpy().view(np.uint64)
-    same = bool(np.array_equal(solo_np, c_b[sample]) and np.array_equal(solo_np, c_p[sample]))
-    same_all = bool(np.array_equal(c_b, c_p))
+    res, counts = {}, {}
+    for mode in modes:
+        res[mode], counts[mode] = serve(mode == "per_request")
+    if len(counts) == 2 and not np.array_equal(counts["batched"], counts["per_request"]):
+        raise CheckFailed(f"rank {rank}: served counts differ between the batched mix and requests counted alone")
+    # a sample of the requests below 1 MiB against the oracle on their bytes
+    small = np.flatnonzero(nbytes < (1 << 20))
+    rng = np.random.default_rng(rank)
+    sample = rng.choice(small, size=min(small.size, oracle_sample), replace=False) if small.size else small
+    for i in sample:
+        w, o = int(tr["width"][i]), int(tr["offset_bytes"][i])
+        host = pool[o: o + int(nbytes[i])].cpu().numpy()
+        ref = oracle.pospopcnt(host, w)
+        for mode in counts:
+            if not np.array_equal(counts[mode][i, :w], ref):
+                raise CheckFailed(f"rank {rank}: request {i} ({mode}) differs from the oracle")
+    return {"requests": int(n), "total_bytes": total, "offered_GBps": total / seconds / 1e9, "modes": res,
+            "checked": (f"every request equal in both modes (per-request = each job counted alone); "
+                        f"{sample.size} requests below 1 MiB equal to the oracle") if len(counts) == 2 else
+                       f"{sample.size} requests below 1 MiB equal to the oracle"}
+
+
+def run_serve(args, world, rank, local):
+    """Serving at one load: the continuous-batching runtime and per-request
+    plain launches on the same trace (see measure_serve), `--serve-runs`
+    times each, median and spread of p50 / p99."""
+    import torch
+    import paper_1911_02696_gb300 as ppc
+    import synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ppc.pospopcnt_init(local)
+    pool = torch.from_numpy(synth.uniform_bytes(100 + rank, 4 << 30)).to(dev)
+    runs = []
+    for r in range(max(1, args.serve_runs)):
+        runs.append(measure_serve(local, rank, args.serve_rate, args.serve_seconds, args.serve_slots,
+                                  args.serve_slots_plain, args.serve_large_mib, args.serve_large_inflight,
+                                  args.serve_max_kib, pool=pool))
     if rank != 0:
         return None
-    return {"metric": "served p99 latency", "value": batched["p99_ms"], "unit": "ms", "n_gpus": world,
-            "steps": 1, "warmup": 1, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "u8/u16/u32", "data": "synthetic",
+
+    def spread(mode, key):
+        v = [r["modes"][mode][key] for r in runs]
+        return {"median": statistics.median(v), "min": min(v), "max": max(v), "runs": v}
+    summary = {mode: {k: spread(mode, k) for k in ("p50_ms", "p99_ms", "p999_ms", "mean_jobs_per_batch")}
+               for mode in ("batched", "per_request")}
+    last = runs[-1]
+    return {"metric": "served p99 latency", "value": summary["batched"]["p99_ms"]["median"], "unit": "ms",
+            "n_gpus": world, "steps": len(runs), "warmup": 1, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8/u16/u32", "data": "synthetic",
             "config": {"workload": f"Poisson {args.serve_rate:g} req/s for {args.serve_seconds:g} s, widths 8/16/32 "
-                                   "(0.2/0.6/0.2), sizes log-uniform 1 KiB..256 MiB, 4 GiB device pool, "
-                                   "budget 64 GiB",
-                       "requests": int(n), "total_GB": round(total / 1e9, 2),
-                       "offered_GBps": round(total / args.serve_seconds / 1e9, 1),
+                                   f"(0.2/0.6/0.2), sizes log-uniform 1 KiB..{args.serve_max_kib:g} KiB, 4 GiB "
+                                   "device pool, budget 64 GiB",
+                       "requests": last["requests"], "total_GB": round(last["total_bytes"] / 1e9, 2),
+                       "offered_GBps": round(last["offered_GBps"], 1),
                        "batched_slots": args.serve_slots, "per_request_slots": args.serve_slots_plain,
                        "large_job_MiB": args.serve_large_mib, "max_large_inflight": args.serve_large_inflight},
-            "continuous_batching": batched, "per_request_plain": plain,
-            "p99_speedup_vs_per_request": round(plain["p99_ms"] / batched["p99_ms"], 2),
-            "results_same_alone_and_in_mix": same, "batched_equals_per_request_all": same_all}
+            "summary": summary,
+            "p99_speedup_vs_per_request": round(summary["per_request"]["p99_ms"]["median"] /
+                                                summary["batched"]["p99_ms"]["median"], 2),
+            "runs": [r["modes"] for r in runs], "checked": last["checked"]}
 
 
 def run_e2e(args, world, rank, local):
@@ -1054,7 +1158,7 @@ def main(argv=None):
                    choices=["u16", "u16_onehot", "u16_sparse", "u16_misaligned", "u8", "u8_onehot", "u32", "u32_onehot",
                             "u64", "popcount", "onehot",
                             "onehot_u16ids", "onehot_u32ids", "sweep", "batched",
-                            "kernels", "autotune", "serve", "e2e", "peaks", "latency_floor", "l2_states",
+                            "kernels", "autotune", "serve", "e2e", "peaks", "l2_states",
                             "ring_ab"])
     p.add_argument("--batched-nseg", type=int, default=20000)
     p.add_argument("--onehot-k", type=int, default=16, choices=range(1, 33), metavar="K",
@@ -1064,7 +1168,10 @@ def main(argv=None):
     p.add_argument("--serve-rate", type=float, default=50000.0)
     p.add_argument("--serve-seconds", type=float, default=60.0)
     p.add_argument("--serve-slots", type=int, default=16, help="batches in flight (continuous batching)")
-    p.add_argument("--serve-slots-plain", type=int, default=64, help="requests in flight (per-request mode)")
+    p.add_argument("--serve-slots-plain", type=int, default=16, help="requests in flight (per-request mode)")
+    p.add_argument("--serve-runs", type=int, default=1, help="serving: runs of each mode (median and spread)")
+    p.add_argument("--serve-max-kib", type=float, default=256 * 1024,
+                   help="serving: largest payload in KiB (sizes log-uniform from 1 KiB)")
     p.add_argument("--serve-large-mib", type=float, default=4.0,
                    help="jobs at least this large are launched on their own")
     p.add_argument("--serve-large-inflight", type=int, default=0,
@@ -1076,6 +1183,10 @@ def main(argv=None):
                    help="run a smaller uniform-bits case of 2^k words (profiling only)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="default workload: skip the batched and serving numbers")
+    p.add_argument("--extras-serve-seconds", type=float, default=5.0,
+                   help="default workload: length of the serving trace per mode")
     args = p.parse_args(argv)
     if args.warmup < 3:
         p.error("--warmup must be >= 3")
@@ -1101,8 +1212,6 @@ def main(argv=None):
             out = run_e2e(args, world, rank, local)
         elif args.workload == "peaks":
             out = run_peaks(args, world, rank, local)
-        elif args.workload == "latency_floor":
-            out = run_latency_floor(args, world, rank, local)
         elif args.workload == "l2_states":
             out = run_l2_states(args, world, rank, local)
         elif args.workload == "ring_ab":
@@ -1115,7 +1224,12 @@ def main(argv=None):
             dist.destroy_process_group()
     if out is not None:
         print(json.dumps(out), flush=True)
+    return 0
 
 
 if __name__ == "__main__":
-    main()
+    try:
+        sys.exit(main())
+    except CheckFailed as exc:
+        print(f"bench: result check failed, no value printed: {exc}", file=sys.stderr, flush=True)
+        sys.exit(3)

@@ -235,16 +235,20 @@ int pospopcnt_batched_checked(const void* d_in, size_t n_words, const int64_t* d
  * of the library, not of the method.  Same arguments, layout and result as
  * pospopcnt_batched; it calls no cudaMalloc, cudaFree or other allocating
  * routine, and needs no pospopcnt_init.  Its scratch (the work-queue state
- * of one launch, 16 bytes, and a word where a bounded device wait records a
- * timeout) lives in a 256-byte static device array that every GPU which
- * loads the library holds until the process exits; a call whose scratch
- * need exceeded 256 bytes would be rejected with POSPOPCNT_ERR_TOO_LARGE
- * (the need does not grow with the input, so every input size fits).  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress, with that device current): make that first
- * call before any stream capture.  Every call on a device shares the one
- * array and clears it on its stream before launching, so calls that overlap
- * on the GPU (other streams, concurrent graph replays) race and give wrong
- * counts: serialise them. */
+ * of one launch and a word where a bounded device wait records that it gave
+ * up, 24 bytes in all) lives in a 256-byte static device array that every
+ * GPU which loads the library holds until the process exits; a call whose
+ * scratch need exceeded 256 bytes would be rejected with
+ * POSPOPCNT_ERR_TOO_LARGE (the need does not grow with the input, so every
+ * input size fits).  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress, with that device current): make
+ * that first call before any stream capture.  Every call on a device shares
+ * the one array and clears all of it on its stream before launching, so
+ * calls that overlap on the GPU (other streams, concurrent graph replays)
+ * race and give wrong counts: serialise them.  A wait that gave up is
+ * reported by pospopcnt_check_device_error(stream), which allocates nothing
+ * either, if it is called before the next call of this form on the device
+ * clears the word. */
 int pospopcnt_batched_noalloc(const void* d_in, const int64_t* d_offsets, size_t nseg, int width,
                               uint64_t* d_counts, cudaStream_t stream);
 
@@ -347,10 +351,14 @@ int pospopcnt_server_get_stats(pospopcnt_server* server, pospopcnt_server_stats*
 int pospopcnt_admission_simulate(uint64_t budget, size_t n, const double* t_arrival, const uint64_t* bytes,
                                  const double* service_s, double* t_admit_out, int* status_out);
 
-/* Synchronises `stream`, reads and clears the device error word (set by a
- * bounded wait that gave up, or by the offsets check of
- * pospopcnt_batched_checked).  Returns POSPOPCNT_OK, POSPOPCNT_ERR_INVALID
- * (bad offsets only) or POSPOPCNT_ERR_TIMEOUT. */
+/* Synchronises `stream`, reads and clears the device error words (set by
+ * a bounded wait that gave up, or by the offsets check of
+ * pospopcnt_batched_checked): the word of the library workspace, if the
+ * workspace exists on the current device, and the word of the
+ * allocation-free batched form, if that form has run there.  Allocates
+ * nothing (a word that does not exist holds no error).  Returns
+ * POSPOPCNT_OK, POSPOPCNT_ERR_INVALID (bad offsets only) or
+ * POSPOPCNT_ERR_TIMEOUT. */
 int pospopcnt_check_device_error(cudaStream_t stream);
 
 /* Host-only planning of the head/body/tail split (§4.1 residual handling):
@@ -392,6 +400,12 @@ int pospopcnt_last_cuda_error(void);
 /* Number of kernels this library has launched in this process (all devices);
  * lets a caller count launches inside a timed region. */
 uint64_t pospopcnt_launch_count(void);
+
+/* Bytes of device memory the library currently holds from its own
+ * cudaMalloc calls in this process (all devices: per-device workspaces,
+ * host-path staging buffers, servers' slot buffers).  Lets a caller check
+ * that a sequence of calls allocated nothing.  Not in the paper. */
+uint64_t pospopcnt_device_bytes_allocated(void);
 
 #ifdef __cplusplus
 }

@@ -27,7 +27,7 @@ __all__ = [
     "pospopcnt_batched", "pospopcnt_batched_checked", "pospopcnt_batched_noalloc",
     "pospopcnt_batched_graph_create", "pospopcnt_graph_launch", "pospopcnt_graph_destroy", "pospopcnt_plain_segments", "pospopcnt_check_device_error", "pospopcnt_plan_split",
     "pospopcnt_get_config", "pospopcnt_set_config", "pospopcnt_autotune", "pospopcnt_strerror",
-    "pospopcnt_last_cuda_error", "pospopcnt_launch_count", "pospopcnt_selftest_timeout", "KERNELS",
+    "pospopcnt_last_cuda_error", "pospopcnt_launch_count", "pospopcnt_device_bytes_allocated", "pospopcnt_selftest_timeout", "KERNELS",
     "Config", "pospopcnt_server_create", "pospopcnt_server_destroy", "pospopcnt_server_submit",
     "pospopcnt_server_poll", "pospopcnt_server_run_trace", "pospopcnt_server_run_trace_timed",
     "pospopcnt_server_get_stats",
@@ -148,6 +148,7 @@ def _declare(lib):
         "pospopcnt_strerror": (ctypes.c_char_p, [i32]),
         "pospopcnt_last_cuda_error": (i32, []),
         "pospopcnt_launch_count": (u64, []),
+        "pospopcnt_device_bytes_allocated": (u64, []),
         "pospopcnt_selftest_timeout": (i32, [u64, vp]),
         "pospopcnt_server_create": (i32, [i32, P(ServerConfig), P(vp)]),
         "pospopcnt_server_destroy": (i32, [vp]),
@@ -522,6 +523,11 @@ def pospopcnt_last_cuda_error() -> int:
 
 def pospopcnt_launch_count() -> int:
     return int(_lib().pospopcnt_launch_count())
+
+
+def pospopcnt_device_bytes_allocated() -> int:
+    """Bytes of device memory the library holds from its own allocations."""
+    return int(_lib().pospopcnt_device_bytes_allocated())
 
 
 def pospopcnt_selftest_timeout(limit_ns: int = 1_000_000, stream=None, device=None) -> None:

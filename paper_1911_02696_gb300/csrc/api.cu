@@ -38,6 +38,7 @@ bool g_bcfg_set[MAX_DEVICES][3] = {};
 constexpr pospopcnt_batched_config BATCHED_DEFAULT = {32768, 2, 2};
 std::mutex g_host_mutex[MAX_DEVICES];
 std::atomic<uint64_t> g_launches{0};
+std::atomic<uint64_t> g_device_bytes{0};
 thread_local int t_last_cuda = 0;
 
 int width_index(int width) {
@@ -147,9 +148,9 @@ int init_locked(int device) {
     if ((e = cudaDeviceGetAttribute(&st.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device)) !=
         cudaSuccess)
       break;
-    if ((e = cudaMalloc(reinterpret_cast<void**>(&st.d_err), 256)) != cudaSuccess) break;
+    if ((e = device_alloc(reinterpret_cast<void**>(&st.d_err), 256)) != cudaSuccess) break;
     if ((e = cudaMemset(st.d_err, 0, 256)) != cudaSuccess) break;
-    if ((e = cudaMalloc(&st.d_queue, size_t(QUEUE_SLOTS) * QUEUE_SLOT_BYTES)) != cudaSuccess) break;
+    if ((e = device_alloc(&st.d_queue, size_t(QUEUE_SLOTS) * QUEUE_SLOT_BYTES)) != cudaSuccess) break;
     if ((e = cudaMemset(st.d_queue, 0, size_t(QUEUE_SLOTS) * QUEUE_SLOT_BYTES)) != cudaSuccess) break;
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) break;
   } while (false);
@@ -171,6 +172,17 @@ int cuda_fail(cudaError_t e) {
 }
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+cudaError_t device_alloc(void** p, size_t bytes) {
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) g_device_bytes.fetch_add(bytes, std::memory_order_relaxed);
+  return e;
+}
+
+void device_free(void* p, size_t bytes) {
+  if (!p) return;
+  if (cudaFree(p) == cudaSuccess) g_device_bytes.fetch_sub(bytes, std::memory_order_relaxed);
+}
 
 DeviceState* current_state(int* status) {
   int dev = -1;
@@ -391,13 +403,13 @@ int pospopcnt_count_host(int width, const void* h_in, size_t n, uint64_t* h_coun
   cudaError_t e = cudaSuccess;
   if (!st->d_acc) {
     for (int i = 0; i < 2; ++i) {
-      if ((e = cudaMalloc(&st->d_stage[i], HOST_STAGE_BYTES)) != cudaSuccess) return cuda_fail(e);
+      if ((e = device_alloc(&st->d_stage[i], HOST_STAGE_BYTES)) != cudaSuccess) return cuda_fail(e);
       if ((e = cudaStreamCreateWithFlags(&st->hstream[i], cudaStreamNonBlocking)) != cudaSuccess)
         return cuda_fail(e);
       if ((e = cudaEventCreateWithFlags(&st->hevent[i], cudaEventDisableTiming)) != cudaSuccess)
         return cuda_fail(e);
     }
-    if ((e = cudaMalloc(reinterpret_cast<void**>(&st->d_acc), 64 * sizeof(uint64_t))) != cudaSuccess)
+    if ((e = device_alloc(reinterpret_cast<void**>(&st->d_acc), 64 * sizeof(uint64_t))) != cudaSuccess)
       return cuda_fail(e);
   }
   cudaStream_t s0 = st->hstream[0], s1 = st->hstream[1];
@@ -619,18 +631,29 @@ int pospopcnt_release_stream(cudaStream_t stream) {
 }
 
 int pospopcnt_check_device_error(cudaStream_t stream) {
-  int rc = POSPOPCNT_OK;
-  DeviceState* st = current_state(&rc);
-  if (!st) return rc;
-  cudaError_t e = cudaStreamSynchronize(stream);
+  // Creates nothing: a word that does not exist on this device cannot hold
+  // an error.
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e);
-  unsigned h = 0;
-  if ((e = cudaMemcpy(&h, st->d_err, sizeof h, cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(e);
-  if (h) {
-    if ((e = cudaMemset(st->d_err, 0, sizeof h)) != cudaSuccess) return cuda_fail(e);
-    return (h & ERR_BIT_BAD_OFFSETS) && !(h & ~unsigned(ERR_BIT_BAD_OFFSETS)) ? POSPOPCNT_ERR_INVALID
-                                                                                : POSPOPCNT_ERR_TIMEOUT;
+  if (dev < 0 || dev >= MAX_DEVICES) return POSPOPCNT_ERR_NOT_INITIALIZED;
+  if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e);
+  unsigned* words[2] = {nullptr, ppc::noalloc_error_word(dev)};
+  {
+    std::lock_guard<std::mutex> lk(g_mutex);
+    if (g_state[dev].ready) words[0] = g_state[dev].d_err;
   }
+  unsigned all = 0;
+  for (unsigned* w : words) {
+    if (!w) continue;
+    unsigned h = 0;
+    if ((e = cudaMemcpy(&h, w, sizeof h, cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(e);
+    if (h && (e = cudaMemset(w, 0, sizeof h)) != cudaSuccess) return cuda_fail(e);
+    all |= h;
+  }
+  if (all)
+    return (all & ERR_BIT_BAD_OFFSETS) && !(all & ~unsigned(ERR_BIT_BAD_OFFSETS)) ? POSPOPCNT_ERR_INVALID
+                                                                                    : POSPOPCNT_ERR_TIMEOUT;
   return POSPOPCNT_OK;
 }
 
@@ -880,5 +903,7 @@ const char* pospopcnt_strerror(int status) {
 int pospopcnt_last_cuda_error(void) { return t_last_cuda; }
 
 uint64_t pospopcnt_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+uint64_t pospopcnt_device_bytes_allocated(void) { return g_device_bytes.load(std::memory_order_relaxed); }
 
 }  // extern "C"

@@ -328,9 +328,9 @@ int launch_batched(const DeviceState& st, const void* d_in, const int64_t* d_off
 // third-party libraries from allocating at all.  pospopcnt_batched and the
 // other entry points allocate the library workspace on their first call;
 // pospopcnt_batched_noalloc never does.  The only scratch the batched
-// kernel needs -- the work-queue state of one launch -- lives in the static
-// array below, which every GPU that loads this library holds until the
-// process exits.
+// kernel needs -- the work-queue state of one launch and the word where a
+// bounded wait records that it gave up -- lives in the static array below,
+// which every GPU that loads this library holds until the process exits.
 //
 // In host code g_noalloc_scratch names a host-side stand-in, not a device
 // address: the device address is looked up with cudaGetSymbolAddress once
@@ -338,6 +338,13 @@ int launch_batched(const DeviceState& st, const void* d_in, const int64_t* d_off
 // passed to the kernel.
 
 namespace ppc {
+
+// What one launch of the allocation-free form keeps in the static array;
+// every call clears all of it on its stream before launching.
+struct NoallocScratch {
+  QueueSlot q;   // work-queue state
+  unsigned err;  // error bits of bounded waits (read by pospopcnt_check_device_error)
+};
 
 constexpr size_t NOALLOC_SCRATCH_BYTES = 256;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
@@ -348,6 +355,13 @@ std::mutex g_noalloc_mutex;
 void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
 int g_noalloc_sms[NOALLOC_MAX_DEVICES] = {};
 }  // namespace
+
+unsigned* noalloc_error_word(int device) {
+  if (device < 0 || device >= NOALLOC_MAX_DEVICES) return nullptr;
+  std::lock_guard<std::mutex> lk(g_noalloc_mutex);
+  if (!g_noalloc_ptr[device]) return nullptr;
+  return &static_cast<NoallocScratch*>(g_noalloc_ptr[device])->err;
+}
 
 }  // namespace ppc
 
@@ -361,8 +375,8 @@ extern "C" int pospopcnt_batched_noalloc(const void* d_in, const int64_t* d_offs
   if (reinterpret_cast<uintptr_t>(d_offsets) % 8 != 0 || reinterpret_cast<uintptr_t>(d_counts) % 8 != 0)
     return POSPOPCNT_ERR_MISALIGNED;
   if (nseg > (size_t(1) << 40)) return POSPOPCNT_ERR_TOO_LARGE;
-  // scratch one launch needs: the queue state (fixed, independent of the input)
-  const size_t need = sizeof(QueueSlot);
+  // scratch one launch needs: fixed, independent of the input
+  const size_t need = sizeof(NoallocScratch);
   if (need > NOALLOC_SCRATCH_BYTES) return POSPOPCNT_ERR_TOO_LARGE;
 
   int dev = -1;
@@ -386,22 +400,23 @@ extern "C" int pospopcnt_batched_noalloc(const void* d_in, const int64_t* d_offs
     scratch = g_noalloc_ptr[dev];
     sms = g_noalloc_sms[dev];
   }
-  // The array keeps the previous call's contents: the queue state must start
-  // at zero, and the rows are overwritten.
+  // The array keeps the previous call's contents: the queue state and the
+  // error word must start at zero, and the rows are overwritten.
   if ((e = cudaMemsetAsync(scratch, 0, need, stream)) != cudaSuccess) return cuda_fail(e);
   if ((e = cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * size_t(width) * nseg, stream)) != cudaSuccess)
     return cuda_fail(e);
   DeviceState st;
   st.sms = sms;
   st.device = dev;
+  NoallocScratch* ns = static_cast<NoallocScratch*>(scratch);
   BatchedArgs a;
   a.base = static_cast<const uint8_t*>(d_in);
   a.offsets = d_offsets;
   a.nseg = nseg;
   a.counts = reinterpret_cast<unsigned long long*>(d_counts);
-  a.q = static_cast<QueueSlot*>(scratch);
+  a.q = &ns->q;
   a.tile_words = uint64_t((16 * 1024) / (width / 8));
-  a.err = reinterpret_cast<unsigned*>(static_cast<char*>(scratch) + 128);  // rest of the static array
+  a.err = &ns->err;
   switch (width) {
     case 8: return launch_batched_k<8>(st, a, stream);
     case 16: return launch_batched_k<16>(st, a, stream);

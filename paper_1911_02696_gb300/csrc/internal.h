@@ -42,6 +42,15 @@ int cuda_fail(cudaError_t e);
 // Counts one kernel launch.
 void note_launch();
 
+// cudaMalloc / cudaFree of device memory the library owns; the bytes held
+// are counted for pospopcnt_device_bytes_allocated.
+cudaError_t device_alloc(void** p, size_t bytes);
+void device_free(void* p, size_t bytes);
+
+// Device address of the allocation-free batched form's error word on
+// `device`, or nullptr if that form has not run there (batched.cu).
+unsigned* noalloc_error_word(int device);
+
 // Head / body / tail split of n words of `width` bits at addr.
 struct Split {
   size_t head_words, body_vectors, tail_words;

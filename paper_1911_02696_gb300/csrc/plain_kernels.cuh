@@ -341,9 +341,19 @@ static int occupancy(Kern kern, int threads, size_t smem) {
   return blocks > 0 ? blocks : 1;
 }
 
-// Per-block u32 partial sums stay exact while one block sees fewer than
-// 2^31 bytes.
-static inline uint64_t min_blocks_for(uint64_t nbytes) { return (nbytes >> 31) + 1; }
+// Smallest grid whose per-thread, per-warp and per-block u32 partial counts
+// stay exact.  A byte adds at most 8 to the one counter of the array
+// popcount (K = 1) and at most 1 to any position's count otherwise, so a
+// block whose share of the input holds at most 2^31 counts per position
+// cannot wrap a u32 partial.  Every family gives a block at most
+// nbytes / grid bytes plus one unit of work (a trip of vectors, a chunk of
+// at most 192 KiB), so with grid >= this value a block's count stays below
+// 2^31 + 8 x 192 Ki < 2^32.
+template <int K>
+static inline uint64_t min_blocks_for(uint64_t nbytes) {
+  constexpr uint64_t per_byte = K == 1 ? 8 : 1;
+  return ((nbytes * per_byte) >> 31) + 1;
+}
 
 // Overwrite semantics: a one-CTA grid stores its counts; a larger grid adds
 // atomically into counts zeroed first by a stream-ordered memset.
@@ -364,7 +374,7 @@ static int launch_csa(const DeviceState& st, PlainArgs a, int bps, bool zero_fir
   const uint64_t cap = uint64_t(st.sms) * uint64_t(std::min(bps > 0 ? bps : occ, occ));
   const uint64_t need = (a.nvec + uint64_t(U) * T - 1) / (uint64_t(U) * T);
   uint64_t grid = std::max<uint64_t>(1, std::min(cap, need));
-  grid = std::max(grid, min_blocks_for(a.nvec * 16));
+  grid = std::max(grid, min_blocks_for<K>(a.nvec * 16));
   if (const int rc = prepare_counts<K>(a, grid, zero_first, stream)) return rc;
   kern<<<unsigned(grid), T, 0, stream>>>(a);
   note_launch();
@@ -380,7 +390,7 @@ static int launch_ballot(const DeviceState& st, PlainArgs a, int bps, bool zero_
   const uint64_t per = uint64_t(32) * U * (T / 32);
   const uint64_t need = (a.nvec + per - 1) / per;
   uint64_t grid = std::max<uint64_t>(1, std::min(cap, need));
-  grid = std::max(grid, min_blocks_for(a.nvec * 16));
+  grid = std::max(grid, min_blocks_for<K>(a.nvec * 16));
   if (const int rc = prepare_counts<K>(a, grid, zero_first, stream)) return rc;
   kern<<<unsigned(grid), T, 0, stream>>>(a);
   note_launch();
@@ -405,7 +415,7 @@ static int launch_tma(const DeviceState& st, const PlainArgs& p, int bps, int st
   const uint64_t cap = uint64_t(st.sms) * uint64_t(std::min(bps > 0 ? bps : occ, occ));
   const uint64_t nchunks = (a.body_bytes + chunk - 1) / chunk;
   uint64_t grid = std::max<uint64_t>(1, std::min(cap, nchunks));
-  grid = std::max(grid, std::min<uint64_t>(nchunks, min_blocks_for(a.body_bytes)));
+  grid = std::max(grid, std::min<uint64_t>(nchunks, min_blocks_for<K>(a.body_bytes)));
   if (const int rc = prepare_counts<K>(a.p, grid, zero_first, stream)) return rc;
   kern<<<unsigned(grid), TMA_THREADS, smem, stream>>>(a);
   note_launch();
@@ -459,7 +469,7 @@ static int launch_csa64(const DeviceState& st, PlainArgs a, int bps, bool zero_f
   const uint64_t cap = uint64_t(st.sms) * uint64_t(std::min(bps > 0 ? bps : occ, occ));
   const uint64_t need = (a.nvec + uint64_t(U) * T - 1) / (uint64_t(U) * T);
   uint64_t grid = std::max<uint64_t>(1, std::min(cap, need));
-  grid = std::max(grid, min_blocks_for(a.nvec * 16));
+  grid = std::max(grid, min_blocks_for<64>(a.nvec * 16));
   if (const int rc = prepare_counts<64>(a, grid, zero_first, stream)) return rc;
   kern<<<unsigned(grid), T, 0, stream>>>(a);
   note_launch();

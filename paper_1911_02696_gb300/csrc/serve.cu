@@ -209,6 +209,7 @@ struct Server {
   DeviceState* st = nullptr;
   std::vector<Slot> slots;
   void* d_pool = nullptr;  // one allocation for every slot's device buffers
+  size_t d_pool_bytes = 0;
   void* h_pool = nullptr;  // one pinned, mapped allocation for every slot's host results
 
   std::mutex in_mu;
@@ -542,7 +543,8 @@ int pospopcnt_server_create(int device, const pospopcnt_server_config* cfg_in, p
   const size_t per_slot = rows_bytes + pieces_pad + 256;  // + the single-job row
   const size_t host_per_slot = rows_bytes + pieces_pad;
   s.slots.resize(size_t(cfg.max_inflight));
-  if ((e = cudaMalloc(&s.d_pool, per_slot * s.slots.size())) != cudaSuccess) rc = ppc::cuda_fail(e);
+  s.d_pool_bytes = per_slot * s.slots.size();
+  if ((e = ppc::device_alloc(&s.d_pool, s.d_pool_bytes)) != cudaSuccess) rc = ppc::cuda_fail(e);
   if (rc == POSPOPCNT_OK && (e = cudaMemset(s.d_pool, 0, per_slot * s.slots.size())) != cudaSuccess)
     rc = ppc::cuda_fail(e);
   if (rc == POSPOPCNT_OK &&
@@ -587,7 +589,7 @@ int pospopcnt_server_destroy(pospopcnt_server* srv) {
   for (ppc::Slot& sl : s.slots) {
     if (sl.stream) cudaStreamSynchronize(sl.stream), cudaStreamDestroy(sl.stream);
   }
-  if (s.d_pool) cudaFree(s.d_pool);
+  ppc::device_free(s.d_pool, s.d_pool_bytes);
   if (s.h_pool) cudaFreeHost(s.h_pool);
   cudaSetDevice(prev);
   delete srv;

@@ -343,3 +343,59 @@ def test_popcount_full():
     got = int(ppc.pospopcnt_popcount(x).cpu()[0])
     ref, _ = oracle.pospopcnt_mt(b, 8)
     assert got == int(ref.sum())
+
+
+# ---------------------------------------------------------------------------
+# 4 GiB, the top of the input-size sweep: counts reach 2^31 per position
+# (u16) and 2^35 in total (popcount), past any 32-bit partial sum
+
+FOUR_GIB_CONFIGS = (None, dict(kernel="csa"), dict(kernel="tma"), dict(kernel="csa", blocks_per_sm=1),
+                    dict(kernel="tma", blocks_per_sm=1, stages=4, chunk_bytes=49152))
+
+
+def _four_gib_u16(words, ref):
+    _, x = _device_slice(words, 0)
+    for cfg in FOUR_GIB_CONFIGS:
+        out = torch.full((16,), SENTINEL, dtype=torch.int64, device="cuda")
+        run_kernel(16, None, x, out, cfg)
+        torch.cuda.synchronize()
+        assert np.array_equal(_as_u64(out), ref), cfg
+    del x
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.slow
+def test_four_gib_u16_uniform():
+    """2^31 u16 words of uniform bits against the oracle."""
+    words = synth.uniform_bits(4, 1 << 31, 16)
+    ref, _ = oracle.pospopcnt_mt(words, 16)
+    assert int(ref.sum()) > 1 << 33
+    _four_gib_u16(words, ref)
+
+
+@pytest.mark.slow
+def test_four_gib_u16_all_ones():
+    """2^31 all-ones u16 words: every position counts 2^31 (closed form, and
+    the oracle on the same words)."""
+    words = np.full(1 << 31, 0xFFFF, dtype=np.uint16)
+    ref, _ = oracle.pospopcnt_mt(words, 16)
+    assert np.array_equal(ref, np.full(16, 1 << 31, dtype=np.uint64))
+    _four_gib_u16(words, ref)
+
+
+@pytest.mark.slow
+def test_four_gib_popcount():
+    """Array popcount of 4 GiB of 0xFF (2^35 set bits) and of 4 GiB of
+    uniform random bytes (the oracle's u8 positional counts summed)."""
+    ones = np.full(1 << 32, 0xFF, dtype=np.uint8)
+    _, x = _device_slice(ones, 0)
+    assert int(ppc.pospopcnt_popcount(x).cpu()[0]) == 1 << 35
+    del x, ones
+    torch.cuda.empty_cache()
+    b = synth.uniform_bytes(6, 1 << 32)
+    _, x = _device_slice(b, 3)
+    got = int(ppc.pospopcnt_popcount(x).cpu()[0])
+    ref, _ = oracle.pospopcnt_mt(b, 8)
+    assert got == int(ref.sum())
+    del x
+    torch.cuda.empty_cache()
