@@ -28,6 +28,12 @@ DeviceState g_state[MAX_DEVICES];
 std::unordered_map<cudaStream_t, int> g_slots[MAX_DEVICES];
 std::vector<int> g_free_slots[MAX_DEVICES];
 int g_next_slot[MAX_DEVICES] = {};
+// Plain-count accumulators, per device: bound to a stream on its first
+// overwriting count, returned with the stream's work-queue slot.  A count
+// on a stream that finds none free takes the memset path.
+std::unordered_map<cudaStream_t, int> g_plain_slots[MAX_DEVICES];
+std::vector<int> g_free_plain[MAX_DEVICES];
+int g_next_plain[MAX_DEVICES] = {};
 pospopcnt_config g_cfg[MAX_DEVICES][4][NCLASSES];
 bool g_cfg_ready[MAX_DEVICES] = {};
 // Batched form, per device and width (8, 16, 32): 32 KiB units, 2 CTAs per
@@ -152,6 +158,8 @@ int init_locked(int device) {
     if ((e = cudaMemset(st.d_err, 0, 256)) != cudaSuccess) break;
     if ((e = device_alloc(&st.d_queue, size_t(QUEUE_SLOTS) * QUEUE_SLOT_BYTES)) != cudaSuccess) break;
     if ((e = cudaMemset(st.d_queue, 0, size_t(QUEUE_SLOTS) * QUEUE_SLOT_BYTES)) != cudaSuccess) break;
+    if ((e = device_alloc(&st.d_plain, size_t(PLAIN_SLOTS) * PLAIN_SLOT_BYTES)) != cudaSuccess) break;
+    if ((e = cudaMemset(st.d_plain, 0, size_t(PLAIN_SLOTS) * PLAIN_SLOT_BYTES)) != cudaSuccess) break;
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) break;
   } while (false);
   if (e != cudaSuccess) rc = cuda_fail(e);
@@ -208,6 +216,51 @@ DeviceState* current_state(int* status) {
   return &g_state[dev];
 }
 
+namespace {
+// The slot of `map` bound to `stream`, binding a free one on first use; -1
+// if all `capacity` slots are bound.  Caller holds g_mutex.
+int bind_slot(std::unordered_map<cudaStream_t, int>& m, std::vector<int>& fl, int& next, int capacity,
+              cudaStream_t stream) {
+  auto it = m.find(stream);
+  if (it != m.end()) return it->second;
+  int slot;
+  if (!fl.empty()) {
+    slot = fl.back();
+    fl.pop_back();
+  } else {
+    if (next >= capacity) return -1;
+    slot = next++;
+  }
+  m.emplace(stream, slot);
+  return slot;
+}
+
+// The batched work-queue slot bound to `stream` on `device`.
+int stream_slot(int device, cudaStream_t stream) {
+  std::lock_guard<std::mutex> lk(g_mutex);
+  return bind_slot(g_slots[device], g_free_slots[device], g_next_slot[device], QUEUE_SLOTS, stream);
+}
+}  // namespace
+
+PlainAcc plain_acc_for(DeviceState& st, cudaStream_t stream) {
+  if (stream == cudaStreamPerThread) return PlainAcc{};
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return PlainAcc{};
+  }
+  if (cs != cudaStreamCaptureStatusNone) return PlainAcc{};
+  int slot;
+  {
+    std::lock_guard<std::mutex> lk(g_mutex);
+    slot = bind_slot(g_plain_slots[st.device], g_free_plain[st.device], g_next_plain[st.device], PLAIN_SLOTS,
+                     stream);
+  }
+  if (slot < 0) return PlainAcc{};
+  char* base = static_cast<char*>(st.d_plain) + size_t(slot) * PLAIN_SLOT_BYTES;
+  return PlainAcc{reinterpret_cast<unsigned long long*>(base), reinterpret_cast<unsigned*>(base + 512)};
+}
+
 Split plan_split(int width, uint64_t addr, size_t n) {
   const uint64_t wb = uint64_t(width / 8);
   const uint64_t nbytes = uint64_t(n) * wb;
@@ -261,16 +314,16 @@ int normalize_config(const DeviceState& st, int width, pospopcnt_config* c) {
 
 template <int K>
 int launch_plain_k(const DeviceState&, const pospopcnt_config&, const void*, size_t, unsigned long long*, bool,
-                   cudaStream_t);
+                   cudaStream_t, const PlainAcc&);
 
 int launch_plain(const DeviceState& st, int width, const pospopcnt_config& cfg, const void* d_in, size_t n,
-                 unsigned long long* d_counts, bool zero_first, cudaStream_t stream) {
+                 unsigned long long* d_counts, bool zero_first, cudaStream_t stream, const PlainAcc& acc) {
   switch (width) {
-    case 1: return launch_plain_k<1>(st, cfg, d_in, n, d_counts, zero_first, stream);
-    case 8: return launch_plain_k<8>(st, cfg, d_in, n, d_counts, zero_first, stream);
-    case 16: return launch_plain_k<16>(st, cfg, d_in, n, d_counts, zero_first, stream);
-    case 32: return launch_plain_k<32>(st, cfg, d_in, n, d_counts, zero_first, stream);
-    case 64: return launch_plain_k<64>(st, cfg, d_in, n, d_counts, zero_first, stream);
+    case 1: return launch_plain_k<1>(st, cfg, d_in, n, d_counts, zero_first, stream, acc);
+    case 8: return launch_plain_k<8>(st, cfg, d_in, n, d_counts, zero_first, stream, acc);
+    case 16: return launch_plain_k<16>(st, cfg, d_in, n, d_counts, zero_first, stream, acc);
+    case 32: return launch_plain_k<32>(st, cfg, d_in, n, d_counts, zero_first, stream, acc);
+    case 64: return launch_plain_k<64>(st, cfg, d_in, n, d_counts, zero_first, stream, acc);
   }
   return POSPOPCNT_ERR_INVALID;
 }
@@ -330,7 +383,8 @@ int count_impl(int width, const pospopcnt_config* cfg_in, bool zero, const void*
   if (!st) return rc;
   pospopcnt_config cfg = cfg_in ? *cfg_in : config_for(*st, width, n);
   if ((rc = normalize_config(*st, width, &cfg)) != POSPOPCNT_OK) return rc;
-  return launch_plain(*st, width, cfg, d_in, n, reinterpret_cast<unsigned long long*>(d_counts), zero, stream);
+  const PlainAcc acc = zero ? plain_acc_for(*st, stream) : PlainAcc{};
+  return launch_plain(*st, width, cfg, d_in, n, reinterpret_cast<unsigned long long*>(d_counts), zero, stream, acc);
 }
 
 }  // namespace
@@ -390,7 +444,8 @@ int pospopcnt_popcount(const void* d_in, size_t nbytes, uint64_t* d_count, cudaS
   // the launch shapes of the 16-bit count serve the single counter too
   pospopcnt_config cfg = tuned_default(16, size_class(uint64_t(nbytes)));
   if ((rc = normalize_config(*st, 16, &cfg)) != POSPOPCNT_OK) return rc;
-  return launch_plain(*st, 1, cfg, d_in, nbytes, reinterpret_cast<unsigned long long*>(d_count), true, stream);
+  return launch_plain(*st, 1, cfg, d_in, nbytes, reinterpret_cast<unsigned long long*>(d_count), true, stream,
+                      plain_acc_for(*st, stream));
 }
 
 int pospopcnt_count_host(int width, const void* h_in, size_t n, uint64_t* h_counts) {
@@ -503,25 +558,8 @@ int batched_impl(const void* d_in, const int64_t* d_offsets, size_t nseg, int wi
   int rc = POSPOPCNT_OK;
   DeviceState* st = current_state(&rc);
   if (!st) return rc;
-  int slot;
-  {
-    std::lock_guard<std::mutex> lk(g_mutex);
-    auto& m = g_slots[st->device];
-    auto it = m.find(stream);
-    if (it != m.end()) {
-      slot = it->second;
-    } else {
-      auto& fl = g_free_slots[st->device];
-      if (!fl.empty()) {
-        slot = fl.back();
-        fl.pop_back();
-      } else {
-        if (g_next_slot[st->device] >= QUEUE_SLOTS) return POSPOPCNT_ERR_TOO_LARGE;
-        slot = g_next_slot[st->device]++;
-      }
-      m.emplace(stream, slot);
-    }
-  }
+  const int slot = stream_slot(st->device, stream);
+  if (slot < 0) return POSPOPCNT_ERR_TOO_LARGE;
   cudaError_t e = cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * size_t(width) * nseg, stream);
   if (e != cudaSuccess) return cuda_fail(e);
   void* q = static_cast<char*>(st->d_queue) + size_t(slot) * QUEUE_SLOT_BYTES;
@@ -561,9 +599,16 @@ void release_slot(int device, cudaStream_t stream) {
   std::lock_guard<std::mutex> lk(g_mutex);
   auto& m = g_slots[device];
   auto it = m.find(stream);
-  if (it == m.end()) return;
-  g_free_slots[device].push_back(it->second);
-  m.erase(it);
+  if (it != m.end()) {
+    g_free_slots[device].push_back(it->second);
+    m.erase(it);
+  }
+  auto& mp = g_plain_slots[device];
+  auto ip = mp.find(stream);
+  if (ip != mp.end()) {
+    g_free_plain[device].push_back(ip->second);
+    mp.erase(ip);
+  }
 }
 }  // namespace
 }  // namespace ppc

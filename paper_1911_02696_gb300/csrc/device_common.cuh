@@ -205,6 +205,27 @@ __device__ __forceinline__ void block_reduce_add(uint32_t (&c)[K], unsigned long
   }
 }
 
+// Overwrite without a memset before the kernel (the last block publishes).
+// Every block has added its counts into acc -- an accumulator owned by the
+// caller's stream, zero between launches -- with block_reduce_add; each
+// block then arrives once on `arrived`, and the block that arrives last
+// moves acc[0..k) into counts and leaves acc and the counter at zero for the
+// next launch on the stream.  Every thread of the block must call it, after
+// its own additions.
+__device__ __forceinline__ void block_publish(unsigned long long* acc, unsigned* arrived,
+                                              unsigned long long* counts, int k) {
+  __shared__ unsigned s_last;
+  __threadfence();  // this thread's additions into acc come before the arrival
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(arrived, 1u) == gridDim.x - 1 ? 1u : 0u;
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    if (int(threadIdx.x) < k) counts[threadIdx.x] = atomicExch(acc + threadIdx.x, 0ull);
+    if (threadIdx.x == 0) atomicExch(arrived, 0u);
+  }
+}
+
 // ---- mbarrier / bulk-copy helpers (inline PTX) ----------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));

@@ -20,6 +20,7 @@ struct DeviceState {
   int smem_optin = 0;
   unsigned* d_err = nullptr;      // device error word
   void* d_queue = nullptr;        // batched work-queue slots (QUEUE_SLOTS x 128 B)
+  void* d_plain = nullptr;        // plain-count accumulators (PLAIN_SLOTS x PLAIN_SLOT_BYTES)
   // host-buffer path
   void* d_stage[2] = {nullptr, nullptr};
   unsigned long long* d_acc = nullptr;
@@ -29,6 +30,8 @@ struct DeviceState {
 
 constexpr int QUEUE_SLOTS = 256;
 constexpr int QUEUE_SLOT_BYTES = 128;
+constexpr int PLAIN_SLOTS = 1024;
+constexpr int PLAIN_SLOT_BYTES = 1024;  // 64 x uint64 accumulator at 0, arrival counter at 512
 constexpr size_t HOST_STAGE_BYTES = size_t(64) << 20;
 
 // Returns the state of the current device, initialising it if needed, or
@@ -57,11 +60,28 @@ struct Split {
 };
 Split plan_split(int width, uint64_t addr, size_t n);
 
+// A stream's accumulator for overwriting counts without a memset: 64
+// uint64 values and an arrival counter, zero between launches on that
+// stream (the last block of each launch leaves them so).
+struct PlainAcc {
+  unsigned long long* acc = nullptr;
+  unsigned* arrived = nullptr;
+};
+
 // Launch of one single-stream count.  zero_first: the counts are
-// overwritten (memset + atomics, or a direct store by a one-CTA grid);
-// otherwise the kernel adds into d_counts.
+// overwritten (a direct store by a one-CTA grid; else, with `acc`, blocks
+// add into the stream's accumulator and the last block writes the counts;
+// else a memset + atomics); otherwise the kernel adds into d_counts.
 int launch_plain(const DeviceState& st, int width, const pospopcnt_config& cfg, const void* d_in,
-                 size_t n, unsigned long long* d_counts, bool zero_first, cudaStream_t stream);
+                 size_t n, unsigned long long* d_counts, bool zero_first, cudaStream_t stream,
+                 const PlainAcc& acc = PlainAcc{});
+
+// The accumulator bound to `stream` on the state's device (binding one of
+// the device's stream slots on first use), or an empty one when the memset
+// path must be taken: the stream is being captured into a CUDA graph (a
+// graph may be replayed on any stream), it is the per-thread default stream
+// (one handle, many streams), or no slot is free.
+PlainAcc plain_acc_for(DeviceState& st, cudaStream_t stream);
 
 // Count of n words in pinned host memory mapped into the device address
 // space (d_in: its device address), adding into d_counts.

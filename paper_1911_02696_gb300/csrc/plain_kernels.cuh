@@ -36,7 +36,17 @@ struct PlainArgs {
   unsigned long long* counts;
   unsigned* err;
   uint32_t store;  // 1: single-CTA grid writes the counts (no memset, no atomics)
+  uint32_t publish;          // 1: blocks add into acc; the last one writes the counts
+  unsigned long long* acc;   // the stream's accumulator (publish), zero between launches
+  unsigned* arrived;         // blocks that have added into acc (publish)
 };
+
+// The block's counts c[0..KC) of positions [base, base + KC): added into
+// the counts (or the stream's accumulator), or stored by a one-CTA grid.
+template <int KC, int NWARPS>
+__device__ __forceinline__ void plain_reduce(uint32_t (&c)[KC], const PlainArgs& a, int base = 0) {
+  block_reduce_add<KC, NWARPS>(c, (a.publish ? a.acc : a.counts) + base, a.store != 0);
+}
 
 template <int K, int NTHREADS>
 __device__ __forceinline__ void count_head_tail(uint32_t (&c)[K], const PlainArgs& a) {
@@ -89,7 +99,8 @@ __global__ void __launch_bounds__(NTHREADS) csa_kernel(PlainArgs a) {
   uint32_t c[K];
   finalize<K, L>(c, top, B);
   count_head_tail<K, NTHREADS>(c, a);
-  block_reduce_add<K, NTHREADS / 32>(c, a.counts, a.store != 0);
+  plain_reduce<K, NTHREADS / 32>(c, a);
+  if (a.publish) block_publish(a.acc, a.arrived, a.counts, K);
 }
 
 // ---------------------------------------------------------------------------
@@ -257,8 +268,9 @@ __global__ void __launch_bounds__(TMA_THREADS) tma_kernel(TmaArgs a) {
 #pragma unroll
   for (int q = 0; q < NC; ++q) {
     if (q) __syncthreads();  // the reduction's shared buffer is reused
-    block_reduce_add<KC, TMA_CWARPS + 1>(c[q], a.p.counts + 32 * q, a.p.store != 0);
+    plain_reduce<KC, TMA_CWARPS + 1>(c[q], a.p, 32 * q);
   }
+  if (a.p.publish) block_publish(a.p.acc, a.p.arrived, a.p.counts, K);
 }
 
 // ---------------------------------------------------------------------------
@@ -287,7 +299,8 @@ __global__ void __launch_bounds__(NTHREADS) ballot_kernel(PlainArgs a) {
 #pragma unroll
   for (int p = 0; p < K; ++p) c[p] = lane == 0 ? acc[p] : 0u;  // every lane holds the warp total
   count_head_tail<K, NTHREADS>(c, a);
-  block_reduce_add<K, NTHREADS / 32>(c, a.counts, a.store != 0);
+  plain_reduce<K, NTHREADS / 32>(c, a);
+  if (a.publish) block_publish(a.acc, a.arrived, a.counts, K);
 }
 
 // ---------------------------------------------------------------------------
@@ -325,9 +338,10 @@ __global__ void __launch_bounds__(NTHREADS) csa64_kernel(PlainArgs a) {
     if (threadIdx.x < a.head_words) count_word64(clo, chi, a.head + threadIdx.x * 8);
     if (threadIdx.x >= 32 && threadIdx.x - 32 < a.tail_words) count_word64(clo, chi, a.tail + (threadIdx.x - 32) * 8);
   }
-  block_reduce_add<32, NTHREADS / 32>(clo, a.counts, a.store != 0);
+  plain_reduce<32, NTHREADS / 32>(clo, a);
   __syncthreads();  // the reduction's shared buffer is reused
-  block_reduce_add<32, NTHREADS / 32>(chi, a.counts + 32, a.store != 0);
+  plain_reduce<32, NTHREADS / 32>(chi, a, 32);
+  if (a.publish) block_publish(a.acc, a.arrived, a.counts, 64);
 }
 
 // ---------------------------------------------------------------------------
@@ -356,11 +370,14 @@ static inline uint64_t min_blocks_for(uint64_t nbytes) {
 }
 
 // Overwrite semantics: a one-CTA grid stores its counts; a larger grid adds
-// atomically into counts zeroed first by a stream-ordered memset.
+// into the stream's accumulator and its last block publishes them (when the
+// caller passed one), else adds atomically into counts zeroed first by a
+// stream-ordered memset.
 template <int K>
 static int prepare_counts(PlainArgs& a, uint64_t grid, bool zero_first, cudaStream_t stream) {
   a.store = (zero_first && grid == 1) ? 1u : 0u;
-  if (zero_first && grid > 1) {
+  a.publish = (zero_first && grid > 1 && a.acc && a.arrived) ? 1u : 0u;
+  if (zero_first && grid > 1 && !a.publish) {
     const cudaError_t e = cudaMemsetAsync(a.counts, 0, sizeof(unsigned long long) * K, stream);
     if (e != cudaSuccess) return cuda_fail(e);
   }
@@ -435,7 +452,8 @@ static int launch_csa_u(const DeviceState& st, const PlainArgs& a, const pospopc
 }
 
 template <int K>
-static PlainArgs make_args(const DeviceState& st, const void* d_in, size_t n, unsigned long long* d_counts) {
+static PlainArgs make_args(const DeviceState& st, const void* d_in, size_t n, unsigned long long* d_counts,
+                           const PlainAcc& acc = PlainAcc{}) {
   constexpr int WB = word_bytes<K>::value;
   const Split sp = plan_split(8 * WB, reinterpret_cast<uint64_t>(d_in), n);
   const uint8_t* base = static_cast<const uint8_t*>(d_in);
@@ -449,6 +467,9 @@ static PlainArgs make_args(const DeviceState& st, const void* d_in, size_t n, un
   a.counts = d_counts;
   a.err = st.d_err;
   a.store = 0;
+  a.publish = 0;
+  a.acc = acc.acc;
+  a.arrived = acc.arrived;
   return a;
 }
 
@@ -479,8 +500,8 @@ static int launch_csa64(const DeviceState& st, PlainArgs a, int bps, bool zero_f
 
 template <int K>
 int launch_plain_k(const DeviceState& st, const pospopcnt_config& cfg, const void* d_in, size_t n,
-                   unsigned long long* d_counts, bool zero_first, cudaStream_t stream) {
-  PlainArgs a = make_args<K>(st, d_in, n, d_counts);
+                   unsigned long long* d_counts, bool zero_first, cudaStream_t stream, const PlainAcc& acc) {
+  PlainArgs a = make_args<K>(st, d_in, n, d_counts, acc);
   if (a.nvec == 0 && a.head_words == 0 && a.tail_words == 0) {
     if (!zero_first) return POSPOPCNT_OK;
     const cudaError_t e = cudaMemsetAsync(d_counts, 0, sizeof(unsigned long long) * K, stream);

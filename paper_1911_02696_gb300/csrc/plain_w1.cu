@@ -3,5 +3,5 @@
 
 namespace ppc {
 template int launch_plain_k<1>(const DeviceState&, const pospopcnt_config&, const void*, size_t,
-                               unsigned long long*, bool, cudaStream_t);
+                               unsigned long long*, bool, cudaStream_t, const PlainAcc&);
 }  // namespace ppc

@@ -3,7 +3,7 @@
 
 namespace ppc {
 template int launch_plain_k<16>(const DeviceState&, const pospopcnt_config&, const void*, size_t,
-                               unsigned long long*, bool, cudaStream_t);
+                               unsigned long long*, bool, cudaStream_t, const PlainAcc&);
 template int launch_plain_sysmem_k<16>(const DeviceState&, const void*, size_t, unsigned long long*,
                                        cudaStream_t);
 }  // namespace ppc

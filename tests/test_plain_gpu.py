@@ -399,3 +399,89 @@ def test_four_gib_popcount():
     assert got == int(ref.sum())
     del x
     torch.cuda.empty_cache()
+
+
+# ---------------------------------------------------------------------------
+# overwrite without a memset: multi-CTA counts add into an accumulator bound
+# to the caller's stream and the last block writes the counts
+
+def test_overwrite_on_many_streams_back_to_back():
+    """Eight streams, each counting its own inputs of every width (u8 / u16 /
+    u32 / u64 and the popcount) back to back, 3 rounds, counts pre-filled with
+    garbage: every result equals the oracle, so no stream's accumulator leaks
+    into another call."""
+    rng = np.random.default_rng(77)
+    streams = [torch.cuda.Stream() for _ in range(8)]
+    jobs = []
+    for i, s in enumerate(streams):
+        for width in (8, 16, 32, 64, 1):
+            nbytes = int(rng.integers(1 << 20, 24 << 20)) // 8 * 8
+            wb = 1 if width == 1 else width // 8
+            words = synth.uniform_bits(i * 10 + width, nbytes // wb, 8 if width == 1 else width)
+            _, x = _device_slice(words, 0)
+            ref = (np.array([oracle.pospopcnt(words, 8).sum()], dtype=np.uint64) if width == 1
+                   else oracle.pospopcnt(words, width))
+            jobs.append((s, width, ref, x))
+    torch.cuda.synchronize()
+    for _ in range(3):
+        outs = []
+        for s, width, ref, x in jobs:
+            out = torch.randint(-2 ** 62, 2 ** 62, (max(width, 1),), dtype=torch.int64, device="cuda")
+            s.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(s):
+                if width == 1:
+                    ppc.pospopcnt_popcount(x, count=out, stream=s)
+                else:
+                    run_kernel(width, None, x, out)
+            outs.append(out)
+        torch.cuda.synchronize()
+        for (s, width, ref, x), out in zip(jobs, outs):
+            assert np.array_equal(_as_u64(out), ref), width
+
+
+def test_overwrite_after_stream_release():
+    """A stream's accumulator returns to the free list with the stream and
+    serves the next stream correctly."""
+    words = synth.uniform_bits(31, 5 << 20, 16)
+    _, x = _device_slice(words, 2)
+    ref = oracle.pospopcnt(words, 16)
+    for _ in range(20):
+        s = torch.cuda.Stream()
+        out = torch.full((16,), -1, dtype=torch.int64, device="cuda")
+        with torch.cuda.stream(s):
+            ppc.pospopcnt_u16(x, counts=out, stream=s)
+            ppc.pospopcnt_u16(x, counts=out, stream=s)
+        s.synchronize()
+        assert np.array_equal(_as_u64(out), ref)
+        ppc.pospopcnt_release_stream(s)
+
+
+def test_graph_replays_on_two_streams():
+    """A captured plain count uses the memset path, so two replays of two
+    graphs capturing the same call may overlap on different streams."""
+    a = synth.uniform_bits(41, 7 << 20, 32)
+    b = synth.uniform_bits(42, 9 << 20, 32)
+    _, xa = _device_slice(a, 4)
+    _, xb = _device_slice(b, 8)
+    oa = torch.empty(32, dtype=torch.int64, device="cuda")
+    ob = torch.empty(32, dtype=torch.int64, device="cuda")
+    ppc.pospopcnt_u32(xa, counts=oa)
+    torch.cuda.synchronize()
+    ga, gb = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+    with torch.cuda.graph(ga):
+        ppc.pospopcnt_u32(xa, counts=oa)
+    with torch.cuda.graph(gb):
+        ppc.pospopcnt_u32(xb, counts=ob)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    for _ in range(10):
+        oa.fill_(-5)
+        ob.fill_(-5)
+        s1.wait_stream(torch.cuda.current_stream())
+        s2.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s1):
+            ga.replay()
+        with torch.cuda.stream(s2):
+            gb.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(_as_u64(oa), oracle.pospopcnt(a, 32))
+        assert np.array_equal(_as_u64(ob), oracle.pospopcnt(b, 32))
