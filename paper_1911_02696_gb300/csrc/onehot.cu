@@ -304,49 +304,83 @@ __device__ __forceinline__ void flush_mad(uint32_t (&top)[K], uint32_t t, uint32
 
 // Per-thread counts of the lookup kernels.  A trip's circuit F_N returns
 // its top register (weight 2^N).  Top registers of consecutive trips are
-// combined as a binary counter of carry-save adders: two of weight 2^N give
-// a sum bit B[N] and a carry of weight 2^(N+1); two such carries give B[N+1]
-// and a carry of weight 2^(N+2), which is flushed with popc.  The flush thus
-// runs once per four trips -- the circuit F_(N+2) without holding
-// 2^(N+2) registers at once.
-template <int LW, int N>
+// combined as a binary counter of carry-save adders, D levels deep: level j
+// holds at most one pending register of weight 2^(N+j); a second one meets
+// it in a CSA whose sum bit goes to B[N+j] and whose carry (weight
+// 2^(N+j+1)) moves up a level, and the carry out of the last level is
+// flushed with popc.  The flush thus runs once per 2^D trips -- the circuit
+// F_(N+D) without holding 2^(N+D) registers at once.  The register-load
+// kernels take two levels; the bulk-copy kernel with one id per register
+// (LW = 32), whose ALU pipe is filled by the circuit, takes four (flush
+// every 16 trips).
+template <int LW>
+struct ring_depth {
+  static constexpr int value = LW == 32 ? 4 : 2;
+};
+
+template <int LW, int N, int D = 2>
 struct PairedCounts {
-  uint32_t B[N + 2];   // B[l] at weight 2^l
-  uint32_t pend0 = 0;  // unpaired top register of a trip (weight 2^N)
-  uint32_t pend1 = 0;  // unpaired carry of a pair of trips (weight 2^(N+1))
+  uint32_t B[N + D];   // B[l] at weight 2^l
+  uint32_t pend[D];    // pend[j]: unpaired register of weight 2^(N+j)
   uint32_t trips = 0;
-  uint32_t top[LW];    // units of 2^(N+2)
+  uint32_t top[LW];    // units of 2^(N+D)
   __device__ __forceinline__ PairedCounts() {
 #pragma unroll
-    for (int l = 0; l < N + 2; ++l) B[l] = 0;
+    for (int l = 0; l < N + D; ++l) B[l] = 0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) pend[j] = 0;
 #pragma unroll
     for (int p = 0; p < LW; ++p) top[p] = 0;
   }
+  // t (weight 2^(N+J)) meets the pending registers of levels J.. up to
+  // level `lvl`, the first one that is free.
+  template <int J>
+  __device__ __forceinline__ void carry_into(uint32_t t, int lvl, uint32_t one) {
+    if constexpr (J == D) {
+      flush_mad<LW>(top, t, one);
+    } else {
+      if (lvl == J) {
+        pend[J] = t;
+      } else {
+        uint32_t h;
+        csa(h, B[N + J], B[N + J], pend[J], t);
+        pend[J] = 0;
+        carry_into<J + 1>(h, lvl, one);
+      }
+    }
+  }
   __device__ __forceinline__ void add_trip(const uint32_t* d, uint32_t one) {
     const uint32_t t = Circuit<N>::run(d, B);
-    if ((trips & 1u) == 0) {
-      pend0 = t;
-    } else {
-      uint32_t h;
-      csa(h, B[N], B[N], pend0, t);
-      pend0 = 0;
-      if ((trips & 2u) == 0) {
-        pend1 = h;
+    if constexpr (D == 2) {
+      if ((trips & 1u) == 0) {
+        pend[0] = t;
       } else {
-        uint32_t h2;
-        csa(h2, B[N + 1], B[N + 1], pend1, h);
-        pend1 = 0;
-        flush_mad<LW>(top, h2, one);
+        uint32_t h;
+        csa(h, B[N], B[N], pend[0], t);
+        pend[0] = 0;
+        if ((trips & 2u) == 0) {
+          pend[1] = h;
+        } else {
+          uint32_t h2;
+          csa(h2, B[N + 1], B[N + 1], pend[1], h);
+          pend[1] = 0;
+          flush_mad<LW>(top, h2, one);
+        }
       }
+    } else {
+      // levels 0 .. lvl-1 hold a pending register (the trailing ones of
+      // `trips`), level lvl is free (lvl == D: the carry is flushed)
+      carry_into<0>(t, __ffs(~trips) - 1, one);
     }
     ++trips;
   }
   __device__ __forceinline__ void finish(uint32_t (&c)[LW]) const {
-    finalize<LW, N + 2>(c, top, B);  // top at 2^(N+2), B[l] at 2^l
+    finalize<LW, N + D>(c, top, B);  // top at 2^(N+D), B[l] at 2^l
 #pragma unroll
-    for (int p = 0; p < LW; ++p) {
-      const uint32_t m = lane_mask<LW>::value << p;
-      c[p] += (static_cast<uint32_t>(__popc(pend0 & m)) << N) + (static_cast<uint32_t>(__popc(pend1 & m)) << (N + 1));
+    for (int j = 0; j < D; ++j) {
+#pragma unroll
+      for (int p = 0; p < LW; ++p)
+        c[p] += static_cast<uint32_t>(__popc(pend[j] & (lane_mask<LW>::value << p))) << (N + j);
     }
   }
 };
@@ -532,7 +566,7 @@ constexpr uint64_t RING_MIN_BYTES = uint64_t(32) << 20;
 template <int LW, int IDB, uint32_t IMM, bool GUARD>
 __device__ __forceinline__ void ring_trip(const uint4* sv, uint32_t base, uint32_t nv, LutRef<IMM> t,
                                           uint32_t lanebase, uint32_t one, uint32_t km,
-                                          PairedCounts<LW, LutTrip<LW, IDB>::N>& acc) {
+                                          PairedCounts<LW, LutTrip<LW, IDB>::N, ring_depth<LW>::value>& acc) {
   constexpr int REGS_PER_VEC = LutTrip<LW, IDB>::REGS_PER_VEC, R = LutTrip<LW, IDB>::R, U = LutTrip<LW, IDB>::U;
   constexpr uint32_t CT = RING_CWARPS * 32;
   uint4 y[U];
@@ -566,7 +600,7 @@ __device__ __forceinline__ void ring_trip(const uint4* sv, uint32_t base, uint32
 template <int LW, int IDB, uint32_t IMM>
 __device__ __forceinline__ uint32_t ring_consume(const OnehotArgs& a, const uint8_t* ring, RingCtl* ctl,
                                                  uint32_t my_chunks, LutRef<IMM> t, uint32_t lanebase,
-                                                 PairedCounts<LW, LutTrip<LW, IDB>::N>& acc) {
+                                                 PairedCounts<LW, LutTrip<LW, IDB>::N, ring_depth<LW>::value>& acc) {
   constexpr uint32_t TRIP = LutTrip<LW, IDB>::U * RING_CWARPS * 32;  // vectors per trip; divides a chunk
   constexpr uint32_t CV = RING_CHUNK / 16;                       // vectors per chunk
   const uint32_t one = a.one, lane = threadIdx.x & 31u;
@@ -665,7 +699,7 @@ __global__ void __launch_bounds__(RING_THREADS, 1) onehot_ring_kernel(OnehotArgs
     uint32_t lanebase;
     asm volatile("mov.u32 %0, %1;" : "=r"(lanebase) : "r"(lane * 4u));
     const uint32_t base = static_cast<uint32_t>(__cvta_generic_to_shared(lut));
-    PairedCounts<LW, N> acc;
+    PairedCounts<LW, N, ring_depth<LW>::value> acc;
     const uint32_t done =
         base == LUT_USUAL_BASE
             ? ring_consume<LW, IDB, LUT_USUAL_BASE>(a, ring, ctl, my_chunks, LutRef<LUT_USUAL_BASE>{base},
