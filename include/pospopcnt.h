@@ -170,14 +170,19 @@ int pospopcnt_batched(const void* d_in, const int64_t* d_offsets, size_t nseg, i
  * the scheduling unit the warps claim from the work queue (4 KiB .. 1 MiB, a
  * multiple of 128); blocks_per_sm: CTAs per SM of the persistent grid (0: as
  * many as fit; more than fit is clamped); ring_stages: depth of each warp's
- * bulk-copy ring, 2, 3 or 4 stages of 4 KiB (0: 2).  Defaults: 32 KiB, 2, 2.
- * The paper's method has no such parameters; they tune the launch of the
- * segmented form (§5 notes that fixed costs dominate small inputs, which
- * these trade against load balance). */
+ * bulk-copy ring, 2, 3 or 4 stages (0: 2); vectors_per_lane: 16-byte words
+ * each lane takes from a stage per trip, 4, 8 or 16 (0: 8), so a stage holds
+ * 2, 4 or 8 KiB and a trip runs the carry-save circuit over 16 or 32
+ * registers per lane (16: twice over 32) -- the analogue of the paper's
+ * 256 B / 512 B / 1 kB circuit choice (§4.1); 16 takes at most 3 stages.
+ * Defaults: 32 KiB, 2, 2, 8.  The paper's method has no launch parameters;
+ * these tune the segmented form (§5 notes that fixed costs dominate small
+ * inputs, which these trade against load balance). */
 typedef struct {
   int unit_bytes;
   int blocks_per_sm;
   int ring_stages;
+  int vectors_per_lane;
 } pospopcnt_batched_config;
 
 /* The configuration pospopcnt_batched (and its checked and graph forms)
@@ -187,7 +192,8 @@ int pospopcnt_batched_get_config(int width, pospopcnt_batched_config* cfg);
  * default).  POSPOPCNT_ERR_INVALID for an out-of-range field. */
 int pospopcnt_batched_set_config(int width, const pospopcnt_batched_config* cfg);
 /* Times every unit size in {4, 8, 16, 32, 64} KiB x CTAs per SM in {1, 2,
- * as many as fit} x ring depth in {2, 3, 4} on the caller's own layout (on
+ * as many as fit} x ring depth in {2, 3, 4} x vectors per lane in {4, 8,
+ * 16} (the valid combinations, 120) on the caller's own layout (on
  * `stream`, synchronous): three rounds interleaved across the candidates,
  * about 2 ms of back-to-back calls per round, median round.  Checks that all
  * of them produce identical rows (POSPOPCNT_ERR_INVALID and nothing

@@ -60,8 +60,9 @@ class Config(ctypes.Structure):
 
 
 class BatchedConfig(ctypes.Structure):
-    """pospopcnt_batched_config: unit_bytes, blocks_per_sm, ring_stages."""
-    _fields_ = [("unit_bytes", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("ring_stages", ctypes.c_int)]
+    """pospopcnt_batched_config: unit_bytes, blocks_per_sm, ring_stages, vectors_per_lane."""
+    _fields_ = [("unit_bytes", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("ring_stages", ctypes.c_int),
+                ("vectors_per_lane", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -365,11 +366,13 @@ def pospopcnt_batched_get_config(width: int, device=None) -> dict:
 
 
 def pospopcnt_batched_set_config(width: int, cfg, device=None) -> None:
-    """Installs cfg (dict with unit_bytes, blocks_per_sm; None: the default)."""
+    """Installs cfg (dict with unit_bytes and optionally blocks_per_sm,
+    ring_stages, vectors_per_lane; None: the default)."""
     torch = _torch()
     ref = None
     if cfg is not None:
-        c = BatchedConfig(int(cfg["unit_bytes"]), int(cfg.get("blocks_per_sm", 0)), int(cfg.get("ring_stages", 0)))
+        c = BatchedConfig(int(cfg["unit_bytes"]), int(cfg.get("blocks_per_sm", 0)), int(cfg.get("ring_stages", 0)),
+                          int(cfg.get("vectors_per_lane", 0)))
         ref = ctypes.byref(c)
     with torch.cuda.device(device if device is not None else torch.cuda.current_device()):
         _check(_lib().pospopcnt_batched_set_config(width, ref), "pospopcnt_batched_set_config")

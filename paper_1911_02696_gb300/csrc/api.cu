@@ -41,7 +41,7 @@ bool g_cfg_ready[MAX_DEVICES] = {};
 // layout), until pospopcnt_batched_set_config/autotune.
 pospopcnt_batched_config g_bcfg[MAX_DEVICES][3] = {};
 bool g_bcfg_set[MAX_DEVICES][3] = {};
-constexpr pospopcnt_batched_config BATCHED_DEFAULT = {32768, 2, 2};
+constexpr pospopcnt_batched_config BATCHED_DEFAULT = {32768, 2, 2, 8};
 std::mutex g_host_mutex[MAX_DEVICES];
 std::atomic<uint64_t> g_launches{0};
 std::atomic<uint64_t> g_device_bytes{0};
@@ -543,7 +543,10 @@ pospopcnt_batched_config batched_config(int device, int width) {
 
 bool batched_config_valid(const pospopcnt_batched_config& c) {
   return c.unit_bytes >= 4096 && c.unit_bytes <= (1 << 20) && c.unit_bytes % 128 == 0 && c.blocks_per_sm >= 0 &&
-         c.blocks_per_sm <= 32 && (c.ring_stages == 0 || (c.ring_stages >= 2 && c.ring_stages <= 4));
+         c.blocks_per_sm <= 32 && (c.ring_stages == 0 || (c.ring_stages >= 2 && c.ring_stages <= 4)) &&
+         (c.vectors_per_lane == 0 || c.vectors_per_lane == 4 || c.vectors_per_lane == 8 ||
+          c.vectors_per_lane == 16) &&
+         !(c.vectors_per_lane == 16 && c.ring_stages == 4);  // 8 warps x 4 x 8 KiB: more than a ring may take
 }
 
 int batched_impl(const void* d_in, const int64_t* d_offsets, size_t nseg, int width, uint64_t* d_counts,
@@ -566,7 +569,7 @@ int batched_impl(const void* d_in, const int64_t* d_offsets, size_t nseg, int wi
   if (checked && (rc = launch_offsets_check(*st, d_offsets, nseg, n_words, q, stream)) != POSPOPCNT_OK) return rc;
   const pospopcnt_batched_config c = cfg ? *cfg : batched_config(st->device, width);
   return launch_batched(*st, d_in, d_offsets, nseg, width, reinterpret_cast<unsigned long long*>(d_counts), q,
-                        c.unit_bytes / (width / 8), c.blocks_per_sm, c.ring_stages, stream);
+                        c.unit_bytes / (width / 8), c.blocks_per_sm, c.ring_stages, c.vectors_per_lane, stream);
 }
 }  // namespace
 }  // namespace ppc
@@ -860,7 +863,11 @@ int pospopcnt_batched_autotune(const void* d_in, const int64_t* d_offsets, size_
   std::vector<pospopcnt_batched_config> cands;
   for (int unit : {4096, 8192, 16384, 32768, 65536})
     for (int bps : {1, 2, 0})
-      for (int stages : {2, 3, 4}) cands.push_back(pospopcnt_batched_config{unit, bps, stages});
+      for (int stages : {2, 3, 4})
+        for (int vpl : {4, 8, 16}) {
+          const pospopcnt_batched_config c{unit, bps, stages, vpl};
+          if (batched_config_valid(c)) cands.push_back(c);
+        }
   const size_t row_words = size_t(width) * nseg;
   std::vector<uint64_t> ref(row_words), got(row_words);
   cudaEvent_t e0 = nullptr, e1 = nullptr;

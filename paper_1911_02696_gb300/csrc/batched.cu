@@ -39,18 +39,30 @@ struct BatchedArgs {
 };
 
 // Per-warp bulk-copy ring: lane 0 streams the 16-byte-aligned body of a long
-// piece into STAGES shared-memory stages of one trip (32 lanes x 8
+// piece into STAGES shared-memory stages of one trip (32 lanes x VPL
 // vectors) each, one mbarrier per stage; the warp counts from shared memory
-// while the next trips are in flight.  Two stages of 4 KiB (64 KiB per CTA)
-// measured faster than three (96 KiB) on the 20,000-segment layout, and
-// faster than three stages of 2 KiB at any CTA count per SM.
+// while the next trips are in flight.  VPL -- the words each lane takes per
+// trip -- sets the copy size (2, 4 or 8 KiB per stage) and the circuit: F_4
+// over 4 vectors per lane, F_5 over 8, and for 16 two runs of F_5 per trip.
+// Two stages of 4 KiB (64 KiB per CTA) measured faster than three (96 KiB)
+// on the 20,000-segment layout, and faster than three stages of 2 KiB at
+// any CTA count per SM.
 constexpr int RING_STAGES = 2;  // default ring depth (a launch may pick 3 or 4)
-constexpr int RING_VPL = 8;
-constexpr int TRIP_VECS = 32 * RING_VPL;
-constexpr int TRIP_BYTES = TRIP_VECS * 16;
-constexpr int RING_MIN_VECS = 2 * TRIP_VECS;  // shorter bodies are loaded directly
-template <int STAGES>
-constexpr size_t bt_ring_smem() { return size_t(BT_WARPS) * STAGES * TRIP_BYTES; }
+constexpr int RING_VPL = 8;     // default vectors per lane per trip (a launch may pick 4 or 16)
+
+template <int VPL>
+struct ring_shape {
+  static constexpr int TRIP_VECS = 32 * VPL;
+  static constexpr int TRIP_BYTES = TRIP_VECS * 16;
+  static constexpr int MIN_VECS = 2 * TRIP_VECS;  // shorter bodies are loaded directly
+  static constexpr int SUB = VPL < 8 ? VPL : 8;   // vectors per lane per circuit run
+  static constexpr int R = 4 * SUB;
+  static constexpr int L = ilog2<R>::value;
+};
+template <int STAGES, int VPL>
+constexpr size_t bt_ring_smem() { return size_t(BT_WARPS) * STAGES * ring_shape<VPL>::TRIP_BYTES; }
+// Largest ring a launch may ask for (8 warps x stages x trip bytes).
+constexpr size_t BT_RING_MAX_SMEM = 196608;
 
 struct WarpRing {
   uint8_t* buf;    // STAGES x TRIP_BYTES
@@ -61,12 +73,12 @@ struct WarpRing {
 // warp_piece_counts with the body streamed through the warp's ring when it
 // is long enough.  Returns false (after recording the error) if a bounded
 // wait gave up; the warp then stops counting.
-template <int K, int STAGES>
+template <int K, int STAGES, int VPL>
 __device__ __forceinline__ bool warp_piece_counts_ring(const uint8_t* base, uint64_t pa, uint64_t pb,
                                                        WarpRing& r, unsigned* err, uint32_t& out) {
+  using RS = ring_shape<VPL>;
   constexpr int WB = K / 8;
-  constexpr int R = 4 * RING_VPL;
-  constexpr int L = ilog2<R>::value;
+  constexpr int TRIP_VECS = RS::TRIP_VECS, TRIP_BYTES = RS::TRIP_BYTES, SUB = RS::SUB, R = RS::R, L = RS::L;
   const int lane = threadIdx.x & 31;
   const uint64_t A = reinterpret_cast<uint64_t>(base) + pa * WB;
   const uint64_t E = reinterpret_cast<uint64_t>(base) + pb * WB;
@@ -75,7 +87,7 @@ __device__ __forceinline__ bool warp_piece_counts_ring(const uint8_t* base, uint
   uint64_t bodyE = E & ~uint64_t(15);
   if (bodyE < bodyA) bodyE = bodyA;
   const uint64_t nvec = (bodyE - bodyA) / 16;
-  if (nvec < RING_MIN_VECS) {
+  if (nvec < RS::MIN_VECS) {
     out = warp_piece_counts<K, BT_VPL>(base, pa, pb);
     return true;
   }
@@ -127,14 +139,17 @@ __device__ __forceinline__ bool warp_piece_counts_ring(const uint8_t* base, uint
     const uint64_t left = nvec - uint64_t(t) * TRIP_VECS;
     const uint32_t nv = uint32_t(left < TRIP_VECS ? left : TRIP_VECS);
     const uint4* sv = reinterpret_cast<const uint4*>(r.buf + size_t(s) * TRIP_BYTES);
-    uint32_t d[R];
 #pragma unroll
-    for (int j = 0; j < RING_VPL; ++j) {
-      const uint32_t idx = uint32_t(j) * 32 + uint32_t(lane);
-      const uint4 x = idx < nv ? sv[idx] : make_uint4(0, 0, 0, 0);
-      d[4 * j + 0] = x.x, d[4 * j + 1] = x.y, d[4 * j + 2] = x.z, d[4 * j + 3] = x.w;
+    for (int h = 0; h < VPL / SUB; ++h) {
+      uint32_t d[R];
+#pragma unroll
+      for (int j = 0; j < SUB; ++j) {
+        const uint32_t idx = uint32_t(h * SUB + j) * 32 + uint32_t(lane);
+        const uint4 x = idx < nv ? sv[idx] : make_uint4(0, 0, 0, 0);
+        d[4 * j + 0] = x.x, d[4 * j + 1] = x.y, d[4 * j + 2] = x.z, d[4 * j + 3] = x.w;
+      }
+      flush<K>(top, Circuit<L>::run(d, B));
     }
-    flush<K>(top, Circuit<L>::run(d, B));
     __syncwarp();  // every lane has read the stage
     if (lane == 0 && t + STAGES < ntrips) issue(t + STAGES);
   }
@@ -149,18 +164,18 @@ __device__ __forceinline__ bool warp_piece_counts_ring(const uint8_t* base, uint
 
 // Counts words [pa, pb) of `base` with the whole warp and adds the result to
 // row[0..K-1]; false if a bounded wait gave up.
-template <int K, int STAGES>
+template <int K, int STAGES, int VPL>
 __device__ __forceinline__ bool warp_count_piece(const uint8_t* base, uint64_t pa, uint64_t pb,
                                                  unsigned long long* row, WarpRing& ring, unsigned* err) {
   constexpr int SH = 5 - ilog2<K>::value;
   const int lane = threadIdx.x & 31;
   uint32_t v = 0;
-  if (!warp_piece_counts_ring<K, STAGES>(base, pa, pb, ring, err, v)) return false;
+  if (!warp_piece_counts_ring<K, STAGES, VPL>(base, pa, pb, ring, err, v)) return false;
   if ((lane & ((1 << SH) - 1)) == 0 && v) atomicAdd(row + (lane >> SH), (unsigned long long)v);
   return true;
 }
 
-template <int K, int STAGES>
+template <int K, int STAGES, int VPL>
 __global__ void __launch_bounds__(BT_THREADS, bt_batched_min_blocks<K>::value) batched_kernel(BatchedArgs a) {
   constexpr int WB = K / 8;
   extern __shared__ __align__(128) uint8_t bt_ring[];
@@ -171,7 +186,7 @@ __global__ void __launch_bounds__(BT_THREADS, bt_batched_min_blocks<K>::value) b
     retire_cta(a.q);
     return;
   }
-  WarpRing ring{bt_ring + size_t(warp) * STAGES * TRIP_BYTES, bt_full[warp], 0};
+  WarpRing ring{bt_ring + size_t(warp) * STAGES * ring_shape<VPL>::TRIP_BYTES, bt_full[warp], 0};
   if (lane == 0) {
     for (int s = 0; s < STAGES; ++s) mbar_init(&ring.full[s], 1);
     mbar_fence_init();
@@ -228,7 +243,7 @@ __global__ void __launch_bounds__(BT_THREADS, bt_batched_min_blocks<K>::value) b
       const int64_t pa = seg_lo > w0 ? seg_lo : w0;
       const int64_t pb = seg_hi < w1 ? seg_hi : w1;
       if (pa < pb) {
-        if (!warp_count_piece<K, STAGES>(a.base, uint64_t(pa), uint64_t(pb), a.counts + s * K, ring, a.err)) {
+        if (!warp_count_piece<K, STAGES, VPL>(a.base, uint64_t(pa), uint64_t(pb), a.counts + s * K, ring, a.err)) {
           failed = true;
           break;
         }
@@ -241,30 +256,47 @@ __global__ void __launch_bounds__(BT_THREADS, bt_batched_min_blocks<K>::value) b
   retire_cta(a.q);
 }
 
-template <int K, int STAGES>
+template <int K, int STAGES, int VPL>
 static int launch_batched_ks(const DeviceState& st, const BatchedArgs& a, cudaStream_t stream,
                             int blocks_per_sm = 0) {
-  auto kern = batched_kernel<K, STAGES>;
-  if (const cudaError_t e = ensure_dynamic_smem<batched_kernel<K, STAGES>>(st.device, int(bt_ring_smem<STAGES>()))) return cuda_fail(e);
+  auto kern = batched_kernel<K, STAGES, VPL>;
+  constexpr size_t smem = bt_ring_smem<STAGES, VPL>();
+  static_assert(smem <= BT_RING_MAX_SMEM, "ring larger than a launch may ask for");
+  if (const cudaError_t e = ensure_dynamic_smem<batched_kernel<K, STAGES, VPL>>(st.device, int(smem)))
+    return cuda_fail(e);
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, BT_THREADS, bt_ring_smem<STAGES>()) != cudaSuccess || occ < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, BT_THREADS, smem) != cudaSuccess || occ < 1)
     occ = 1;
   const int bps = blocks_per_sm > 0 && blocks_per_sm < occ ? blocks_per_sm : occ;
   const unsigned grid = unsigned(st.sms) * unsigned(bps);
-  kern<<<grid, BT_THREADS, bt_ring_smem<STAGES>(), stream>>>(a);
+  kern<<<grid, BT_THREADS, smem, stream>>>(a);
   note_launch();
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? POSPOPCNT_OK : cuda_fail(e);
 }
 
-// ring_stages: the per-warp ring depth, 2 (default, also for 0), 3 or 4.
+template <int K, int VPL>
+static int launch_batched_kv(const DeviceState& st, const BatchedArgs& a, cudaStream_t stream, int blocks_per_sm,
+                             int ring_stages) {
+  switch (ring_stages) {
+    case 3: return launch_batched_ks<K, 3, VPL>(st, a, stream, blocks_per_sm);
+    case 4:
+      if constexpr (bt_ring_smem<4, VPL>() <= BT_RING_MAX_SMEM) return launch_batched_ks<K, 4, VPL>(st, a, stream, blocks_per_sm);
+      return POSPOPCNT_ERR_INVALID;
+    default: return launch_batched_ks<K, RING_STAGES, VPL>(st, a, stream, blocks_per_sm);
+  }
+}
+
+// ring_stages: the per-warp ring depth, 2 (default, also for 0), 3 or 4;
+// vpl: vectors per lane per trip, 4, 8 (default, also for 0) or 16 (16 with
+// at most 3 stages).
 template <int K>
 static int launch_batched_k(const DeviceState& st, const BatchedArgs& a, cudaStream_t stream, int blocks_per_sm = 0,
-                            int ring_stages = 0) {
-  switch (ring_stages) {
-    case 3: return launch_batched_ks<K, 3>(st, a, stream, blocks_per_sm);
-    case 4: return launch_batched_ks<K, 4>(st, a, stream, blocks_per_sm);
-    default: return launch_batched_ks<K, RING_STAGES>(st, a, stream, blocks_per_sm);
+                            int ring_stages = 0, int vpl = 0) {
+  switch (vpl) {
+    case 4: return launch_batched_kv<K, 4>(st, a, stream, blocks_per_sm, ring_stages);
+    case 16: return launch_batched_kv<K, 16>(st, a, stream, blocks_per_sm, ring_stages);
+    default: return launch_batched_kv<K, RING_VPL>(st, a, stream, blocks_per_sm, ring_stages);
   }
 }
 
@@ -299,7 +331,7 @@ int launch_offsets_check(const DeviceState& st, const int64_t* d_offsets, size_t
 
 int launch_batched(const DeviceState& st, const void* d_in, const int64_t* d_offsets, size_t nseg,
                    int width, unsigned long long* d_counts, void* queue_slot, int tile_words,
-                   int blocks_per_sm, int ring_stages, cudaStream_t stream) {
+                   int blocks_per_sm, int ring_stages, int vpl, cudaStream_t stream) {
   BatchedArgs a;
   a.base = static_cast<const uint8_t*>(d_in);
   a.offsets = d_offsets;
@@ -309,9 +341,9 @@ int launch_batched(const DeviceState& st, const void* d_in, const int64_t* d_off
   a.tile_words = uint64_t(tile_words);
   a.err = st.d_err;
   switch (width) {
-    case 8: return launch_batched_k<8>(st, a, stream, blocks_per_sm, ring_stages);
-    case 16: return launch_batched_k<16>(st, a, stream, blocks_per_sm, ring_stages);
-    case 32: return launch_batched_k<32>(st, a, stream, blocks_per_sm, ring_stages);
+    case 8: return launch_batched_k<8>(st, a, stream, blocks_per_sm, ring_stages, vpl);
+    case 16: return launch_batched_k<16>(st, a, stream, blocks_per_sm, ring_stages, vpl);
+    case 32: return launch_batched_k<32>(st, a, stream, blocks_per_sm, ring_stages, vpl);
   }
   return POSPOPCNT_ERR_INVALID;
 }

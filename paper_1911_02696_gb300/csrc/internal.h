@@ -94,10 +94,11 @@ int normalize_config(const DeviceState& st, int width, pospopcnt_config* cfg);
 // Launch of the batched kernel (counts zeroed by the caller).  tile_words:
 // words per scheduling unit (a multiple of 128 bytes); blocks_per_sm: CTAs
 // per SM of the persistent grid (0, or more than fit: as many as fit);
-// ring_stages: per-warp ring depth 2, 3 or 4 (0: 2).
+// ring_stages: per-warp ring depth 2, 3 or 4 (0: 2); vpl: vectors per lane
+// per trip 4, 8 or 16 (0: 8; 16 takes at most 3 stages).
 int launch_batched(const DeviceState& st, const void* d_in, const int64_t* d_offsets, size_t nseg,
                    int width, unsigned long long* d_counts, void* queue_slot, int tile_words,
-                   int blocks_per_sm, int ring_stages, cudaStream_t stream);
+                   int blocks_per_sm, int ring_stages, int vpl, cudaStream_t stream);
 
 // Checks offsets on the device before a batched launch on the same slot:
 // a violation makes that launch count nothing and sets the error word.

@@ -122,10 +122,11 @@ def test_argument_checks_need_no_device():
     cfg = ppc.BatchedConfig(16384, 0, 0)
     assert lib.pospopcnt_batched_get_config(12, ctypes.byref(cfg)) == 1
     assert lib.pospopcnt_batched_get_config(16, None) == 1
-    for unit, bps, stages in ((2048, 0, 0), (4096 + 64, 0, 0), (2 << 20, 0, 0), (4096, -1, 0), (4096, 33, 0),
-                              (4096, 0, 1), (4096, 0, 5)):
-        bad = ppc.BatchedConfig(unit, bps, stages)
-        assert lib.pospopcnt_batched_set_config(16, ctypes.byref(bad)) == 1, (unit, bps, stages)
+    for unit, bps, stages, vpl in ((2048, 0, 0, 0), (4096 + 64, 0, 0, 0), (2 << 20, 0, 0, 0), (4096, -1, 0, 0),
+                                   (4096, 33, 0, 0), (4096, 0, 1, 0), (4096, 0, 5, 0), (4096, 0, 0, 2),
+                                   (4096, 0, 0, 12), (4096, 0, 0, 32), (4096, 0, 4, 16)):
+        bad = ppc.BatchedConfig(unit, bps, stages, vpl)
+        assert lib.pospopcnt_batched_set_config(16, ctypes.byref(bad)) == 1, (unit, bps, stages, vpl)
     assert lib.pospopcnt_batched_set_config(64, None) == 1
     assert lib.pospopcnt_batched_autotune(good, good, 3, 16, good, None, None, None) == 1
     assert lib.pospopcnt_batched_autotune(good, good, 0, 16, good, ctypes.byref(cfg), None, None) == 1

@@ -211,18 +211,58 @@ def test_batched_autotune_and_config():
         assert np.array_equal(got.cpu().numpy().view(np.uint64), ref)
         for cfg in ({"unit_bytes": 4096, "blocks_per_sm": 1}, {"unit_bytes": 1 << 20, "blocks_per_sm": 32},
                     {"unit_bytes": 8192 + 128, "blocks_per_sm": 0}, {"unit_bytes": 16384, "ring_stages": 3},
-                    {"unit_bytes": 65536, "blocks_per_sm": 1, "ring_stages": 4}):
+                    {"unit_bytes": 65536, "blocks_per_sm": 1, "ring_stages": 4},
+                    {"unit_bytes": 16384, "vectors_per_lane": 4, "ring_stages": 4},
+                    {"unit_bytes": 131072, "vectors_per_lane": 16, "ring_stages": 3}):
             ppc.pospopcnt_batched_set_config(16, cfg)
             got = ppc.pospopcnt_batched(x, d_off, 16)
             assert np.array_equal(got.cpu().numpy().view(np.uint64), ref), cfg
         for bad in ({"unit_bytes": 2048}, {"unit_bytes": 4096 + 64}, {"unit_bytes": 2 << 20},
                     {"unit_bytes": 4096, "blocks_per_sm": -1}, {"unit_bytes": 4096, "blocks_per_sm": 33},
-                    {"unit_bytes": 4096, "ring_stages": 1}, {"unit_bytes": 4096, "ring_stages": 5}):
+                    {"unit_bytes": 4096, "ring_stages": 1}, {"unit_bytes": 4096, "ring_stages": 5},
+                    {"unit_bytes": 4096, "vectors_per_lane": 2}, {"unit_bytes": 4096, "vectors_per_lane": 32},
+                    {"unit_bytes": 4096, "vectors_per_lane": 16, "ring_stages": 4}):
             with pytest.raises(ppc.PospopcntError):
                 ppc.pospopcnt_batched_set_config(16, bad)
     finally:
         ppc.pospopcnt_batched_set_config(16, None)
-    assert ppc.pospopcnt_batched_get_config(16) == {"unit_bytes": 32768, "blocks_per_sm": 2, "ring_stages": 2}
+    assert ppc.pospopcnt_batched_get_config(16) == {"unit_bytes": 32768, "blocks_per_sm": 2, "ring_stages": 2,
+                                                    "vectors_per_lane": 8}
+
+
+@pytest.mark.parametrize("width", (8, 16, 32))
+def test_every_autotune_candidate_matches_oracle(width):
+    """Every configuration the autotuner may pick -- unit size x CTAs per SM
+    x ring depth x vectors per lane, 120 in all -- gives the oracle's rows
+    on a layout with empty, one-word, misaligned and ring-length segments."""
+    rng = np.random.default_rng(20 + width)
+    lens = rng.integers(0, 60000, size=240).astype(np.int64)
+    lens[::7] = 0
+    lens[3::11] = 1
+    lens[5::13] = 300000  # long enough for every ring shape, several trips
+    off = synth.offsets_from_lengths(lens, start=3)
+    words = synth.uniform_bits(30 + width, int(off[-1]) + 5, width)
+    _, x = _dev(words, width // 8)
+    d_off = torch.from_numpy(off).cuda()
+    ref = oracle.pospopcnt_segments(words, off, width)
+    n = 0
+    try:
+        for unit in (4096, 8192, 16384, 32768, 65536):
+            for bps in (1, 2, 0):
+                for stages in (2, 3, 4):
+                    for vpl in (4, 8, 16):
+                        if vpl == 16 and stages == 4:
+                            continue
+                        cfg = {"unit_bytes": unit, "blocks_per_sm": bps, "ring_stages": stages,
+                               "vectors_per_lane": vpl}
+                        ppc.pospopcnt_batched_set_config(width, cfg)
+                        got = torch.full((off.size - 1, width), -1, dtype=torch.int64, device="cuda")
+                        ppc.pospopcnt_batched(x, d_off, width, counts=got)
+                        assert np.array_equal(got.cpu().numpy().view(np.uint64), ref), cfg
+                        n += 1
+    finally:
+        ppc.pospopcnt_batched_set_config(width, None)
+    assert n == 120
 
 
 def test_stream_slots_are_released_and_reused():
