@@ -1228,9 +1228,15 @@ def main(argv=None):
     return 0
 
 
-if __name__ == "__main__":
+def cli(argv=None) -> int:
+    """main() with the result check's verdict as the exit status: a timed
+    result that differs from the oracle's prints no value and returns 3."""
     try:
-        sys.exit(main())
+        return main(argv)
     except CheckFailed as exc:
         print(f"bench: result check failed, no value printed: {exc}", file=sys.stderr, flush=True)
-        sys.exit(3)
+        return 3
+
+
+if __name__ == "__main__":
+    sys.exit(cli())

@@ -20,14 +20,21 @@
  *     counters; the *_accumulate entry point keeps that form).  Counts are
  *     exact uint64 values; every result is bit-exact.
  *   - Entry points taking a cudaStream_t are asynchronous on that stream:
- *     they enqueue at most a memset of the outputs and one counting kernel
- *     (a count that fits one CTA stores its result without the memset; the
- *     checked batched form adds a small offsets check), copy nothing between
- *     host and device and never synchronise.  The caller owns every buffer;
- *     the library never frees, retains or writes d_in.
+ *     they enqueue at most a memset of the outputs and one counting kernel,
+ *     copy nothing between host and device and never synchronise.  A plain
+ *     count overwrites its outputs without a memset: a count that fits one
+ *     CTA stores them, a larger one adds into an accumulator bound to the
+ *     stream and its last block writes them (while the stream is being
+ *     captured into a CUDA graph, and on cudaStreamPerThread, the outputs
+ *     are zeroed by a memset first, so a graph may be replayed on any
+ *     stream).  The batched and one-hot forms zero their outputs with a
+ *     memset; the checked batched form adds a small offsets check.  The
+ *     caller owns every buffer; the library never frees, retains or writes
+ *     d_in.
  *   - The first call on a device allocates the library's per-device
- *     workspace (error word, work-queue slots); pospopcnt_init() does that
- *     up front, after which the asynchronous calls allocate nothing.
+ *     workspace (error word, work-queue slots, per-stream accumulators);
+ *     pospopcnt_init() does that up front, after which the asynchronous
+ *     calls allocate nothing.
  *   - Errors are returned as pospopcnt_status values before anything is
  *     enqueued; a failing CUDA call yields POSPOPCNT_ERR_CUDA and its
  *     cudaError_t is kept for pospopcnt_last_cuda_error().
@@ -82,8 +89,8 @@ typedef struct {
  * byte is read exactly once, so its lines need not stay in L2). */
 #define POSPOPCNT_FLAG_EVICT_FIRST 1
 
-/* Creates the per-device state of `device` (error word, queue slots, SM
- * count).  Idempotent.  Makes `device` current only for the duration of
+/* Creates the per-device state of `device` (error word, queue slots,
+ * per-stream accumulators of the plain count, SM count).  Idempotent.  Makes `device` current only for the duration of
  * the call. */
 int pospopcnt_init(int device);
 
@@ -206,10 +213,11 @@ int pospopcnt_batched_autotune(const void* d_in, const int64_t* d_offsets, size_
 
 /* Returns the work-queue slot that batched calls on `stream` hold on the
  * current device (the library binds one of its 256 slots per device to
- * each stream on that stream's first batched call).  Call it before
- * destroying a stream that made batched calls, once none of its work is in
- * flight; a later batched call on the stream binds a slot again.  OK if
- * the stream holds none.  (pospopcnt_graph_destroy releases its graph's slot
+ * each stream on that stream's first batched call), and the accumulator its
+ * plain counts hold (one of 1024; a stream that finds none free counts
+ * through a memset instead).  Call it before destroying a stream that made
+ * such calls, once none of its work is in flight; a later call on the
+ * stream binds them again.  OK if the stream holds none.  (pospopcnt_graph_destroy releases its graph's slot
  * itself.)  Not in the paper: bookkeeping of the segmented form. */
 int pospopcnt_release_stream(cudaStream_t stream);
 
