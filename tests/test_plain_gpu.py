@@ -485,3 +485,43 @@ def test_graph_replays_on_two_streams():
         torch.cuda.synchronize()
         assert np.array_equal(_as_u64(oa), oracle.pospopcnt(a, 32))
         assert np.array_equal(_as_u64(ob), oracle.pospopcnt(b, 32))
+
+
+def test_per_thread_default_stream_from_several_threads():
+    """cudaStreamPerThread is one handle for a different stream in every
+    host thread, so counts on it must not share a stream accumulator: four
+    threads count different inputs on it at once, each repeatedly, and every
+    result equals the oracle."""
+    import ctypes
+    import threading
+    lib = ppc.load()
+    per_thread = ctypes.c_void_p(2)  # cudaStreamPerThread
+    inputs = []
+    for i in range(4):
+        words = synth.uniform_bits(90 + i, (6 << 20) + 131 * i, 16)
+        _, x = _device_slice(words, 2 * i)
+        inputs.append((x, oracle.pospopcnt(words, 16)))
+    outs = [torch.full((16,), -1, dtype=torch.int64, device="cuda") for _ in inputs]
+    torch.cuda.synchronize()
+    errors = []
+
+    def work(i):
+        try:
+            torch.cuda.set_device(0)
+            x, ref = inputs[i]
+            for _ in range(25):
+                rc = lib.pospopcnt_u16(ctypes.c_void_p(x.data_ptr()), x.numel() // 2,
+                                       ctypes.c_void_p(outs[i].data_ptr()), per_thread)
+                assert rc == 0, ppc.pospopcnt_strerror(rc)
+        except Exception as exc:  # reported on the main thread
+            errors.append(exc)
+
+    threads = [threading.Thread(target=work, args=(i,)) for i in range(4)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    torch.cuda.synchronize()
+    assert not errors, errors
+    for (x, ref), out in zip(inputs, outs):
+        assert np.array_equal(_as_u64(out), ref)
