@@ -212,18 +212,24 @@ __device__ __forceinline__ void block_reduce_add(uint32_t (&c)[K], unsigned long
 // moves acc[0..k) into counts and leaves acc and the counter at zero for the
 // next launch on the stream.  Every thread of the block must call it, after
 // its own additions.
-__device__ __forceinline__ void block_publish(unsigned long long* acc, unsigned* arrived,
-                                              unsigned long long* counts, int k) {
-  __shared__ unsigned s_last;
+// `last` is a word of shared memory the block may use for the verdict.
+__device__ __forceinline__ void block_publish_via(unsigned long long* acc, unsigned* arrived,
+                                                  unsigned long long* counts, int k, volatile unsigned* last) {
   __threadfence();  // this thread's additions into acc come before the arrival
   __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(arrived, 1u) == gridDim.x - 1 ? 1u : 0u;
+  if (threadIdx.x == 0) *last = atomicAdd(arrived, 1u) == gridDim.x - 1 ? 1u : 0u;
   __syncthreads();
-  if (s_last) {
+  if (*last) {
     __threadfence();
     if (int(threadIdx.x) < k) counts[threadIdx.x] = atomicExch(acc + threadIdx.x, 0ull);
     if (threadIdx.x == 0) atomicExch(arrived, 0u);
   }
+}
+
+__device__ __forceinline__ void block_publish(unsigned long long* acc, unsigned* arrived,
+                                              unsigned long long* counts, int k) {
+  __shared__ unsigned s_last;
+  block_publish_via(acc, arrived, counts, k, &s_last);
 }
 
 // ---- mbarrier / bulk-copy helpers (inline PTX) ----------------------------

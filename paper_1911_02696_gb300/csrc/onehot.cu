@@ -34,6 +34,9 @@ struct OnehotArgs {
   uint32_t store;
   uint32_t one;  // 1: multiplier of the FMA-pipe additions in the lookup kernels
   unsigned* err;  // device error word (bounded waits of the ring kernel)
+  uint32_t publish;         // 1: blocks add into acc; the last one writes the counts
+  unsigned long long* acc;  // the stream's accumulator (publish), zero between launches
+  unsigned* arrived;        // blocks that have added into acc (publish)
 };
 
 // The j-th id of a 16-byte vector of IDB-byte ids (j known at compile time),
@@ -113,7 +116,8 @@ __global__ void __launch_bounds__(NTHREADS) onehot_kernel(OnehotArgs a) {
       count_word<LW>(c, id < k ? 1u << id : 0u);
     }
   }
-  block_reduce_add<LW, NTHREADS / 32>(c, a.counts, a.store != 0, int(k));
+  block_reduce_add<LW, NTHREADS / 32>(c, a.publish ? a.acc : a.counts, a.store != 0, int(k));
+  if (a.publish) block_publish(a.acc, a.arrived, a.counts, int(k));
 }
 
 // 8- and 16-bit ids: the one-hot lane comes from a lookup table in shared
@@ -388,10 +392,13 @@ struct PairedCounts {
 // The block's counts: each warp reduces its lanes' counters, warps
 // [0, CWARPS) leave their sums in `red` (CWARPS x LW words of shared memory
 // that no thread reads or writes any more), and threads 0..k-1 add them
-// into counts[p] with one atomic each, or store them when the grid is one
-// CTA.  Every thread of the block calls it.
+// into counts[p] (or the stream's accumulator, whose last block then writes
+// the counts; `last` is a free word of shared memory for that verdict) with
+// one atomic each, or store them when the grid is one CTA.  Every thread of
+// the block calls it.
 template <int LW, int CWARPS>
-__device__ __forceinline__ void reduce_counts_in(uint32_t* red, uint32_t (&c)[LW], const OnehotArgs& a) {
+__device__ __forceinline__ void reduce_counts_in(uint32_t* red, uint32_t (&c)[LW], const OnehotArgs& a,
+                                                 volatile unsigned* last) {
   constexpr int SH = 5 - ilog2<LW>::value;
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const uint32_t vsum = warp_reduce_positions<LW>(c);
@@ -405,8 +412,9 @@ __device__ __forceinline__ void reduce_counts_in(uint32_t* red, uint32_t (&c)[LW
     if (a.store)
       a.counts[threadIdx.x] = sum;
     else if (sum)
-      atomicAdd(a.counts + threadIdx.x, sum);
+      atomicAdd((a.publish ? a.acc : a.counts) + threadIdx.x, sum);
   }
+  if (a.publish) block_publish_via(a.acc, a.arrived, a.counts, int(a.k), last);
 }
 
 // A trip is U = 4 vectors per thread (2 for one 8-bit id per register),
@@ -502,7 +510,8 @@ __global__ void __launch_bounds__(NTHREADS, 3) onehot_lut_kernel(OnehotArgs a) {
   }
   // block reduction in the table's memory, free once every warp is past its
   // last lookup
-  reduce_counts_in<LW, NTHREADS / 32>(reinterpret_cast<uint32_t*>(lut), c, a);
+  reduce_counts_in<LW, NTHREADS / 32>(reinterpret_cast<uint32_t*>(lut), c, a,
+                                      reinterpret_cast<unsigned*>(lut + LUT_BYTES - 4));
 }
 
 template <int LW, int IDB>
@@ -519,7 +528,8 @@ static int launch_onehot_lut(const DeviceState& st, OnehotArgs a, cudaStream_t s
   uint64_t grid = std::max<uint64_t>(1, std::min(cap, need));
   grid = std::max<uint64_t>(grid, ((a.nvec * 16) >> 31) + 1);  // per-CTA u32 partials stay exact
   a.store = grid == 1 ? 1u : 0u;
-  if (grid > 1) {
+  a.publish = grid > 1 && a.acc && a.arrived ? 1u : 0u;
+  if (grid > 1 && !a.publish) {
     const cudaError_t e = cudaMemsetAsync(a.counts, 0, sizeof(unsigned long long) * a.k, stream);
     if (e != cudaSuccess) return cuda_fail(e);
   }
@@ -548,6 +558,7 @@ struct RingCtl {
   uint32_t issued;                 // chunks the producer issued
   uint32_t abort;
   uint32_t consumed[RING_CWARPS];  // chunks each consumer warp finished
+  uint32_t last;                   // this block arrived last on the stream's accumulator
 };
 
 constexpr size_t RING_SMEM = size_t(LUT_BYTES) + size_t(RING_STAGES) * RING_CHUNK + sizeof(RingCtl);
@@ -733,7 +744,7 @@ __global__ void __launch_bounds__(RING_THREADS, 1) onehot_ring_kernel(OnehotArgs
     }
   }
   // block reduction in the table's memory; the producer warp holds no counts
-  reduce_counts_in<LW, RING_CWARPS>(reinterpret_cast<uint32_t*>(lut), c, a);
+  reduce_counts_in<LW, RING_CWARPS>(reinterpret_cast<uint32_t*>(lut), c, a, &ctl->last);
 }
 
 template <int LW, int IDB>
@@ -746,7 +757,8 @@ static int launch_onehot_ring(const DeviceState& st, OnehotArgs a, cudaStream_t 
   // a consumer warp's u32 partials stay exact: at most 2^31 ids per warp
   grid = std::max(grid, std::min<uint64_t>(nchunks, ((a.nvec * 16) >> 35) + 1));
   a.store = grid == 1 ? 1u : 0u;
-  if (grid > 1) {
+  a.publish = grid > 1 && a.acc && a.arrived ? 1u : 0u;
+  if (grid > 1 && !a.publish) {
     const cudaError_t e = cudaMemsetAsync(a.counts, 0, sizeof(unsigned long long) * a.k, stream);
     if (e != cudaSuccess) return cuda_fail(e);
   }
@@ -768,7 +780,8 @@ static int launch_onehot(const DeviceState& st, OnehotArgs a, cudaStream_t strea
   uint64_t grid = std::max<uint64_t>(1, std::min(cap, need));
   grid = std::max<uint64_t>(grid, ((a.nvec * 16) >> 31) + 1);  // per-CTA u32 partials stay exact
   a.store = grid == 1 ? 1u : 0u;
-  if (grid > 1) {
+  a.publish = grid > 1 && a.acc && a.arrived ? 1u : 0u;
+  if (grid > 1 && !a.publish) {
     const cudaError_t e = cudaMemsetAsync(a.counts, 0, sizeof(unsigned long long) * a.k, stream);
     if (e != cudaSuccess) return cuda_fail(e);
   }
@@ -823,6 +836,10 @@ extern "C" int pospopcnt_onehot_counts(const void* d_ids, size_t n, int id_bytes
   a.store = 0;
   a.one = 1;
   a.err = st->d_err;
+  const PlainAcc acc = plain_acc_for(*st, stream);
+  a.publish = 0;
+  a.acc = acc.acc;
+  a.arrived = acc.arrived;
   if (n == 0) {
     const cudaError_t e = cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * size_t(k), stream);
     return e == cudaSuccess ? POSPOPCNT_OK : cuda_fail(e);

@@ -138,3 +138,37 @@ def test_full_u8_ids_zipf16():
     got = _run(ids, 16)
     assert int(got.sum()) == 1 << 31
     assert np.array_equal(got, oracle.onehot_counts(ids, 16))
+
+
+def test_overwrite_on_streams_mixed_with_plain_counts():
+    """One-hot counts overwrite their outputs through the stream's
+    accumulator, which plain counts on the same stream share: six streams
+    each alternate one-hot counts (every id width, both 8-bit-id kernels) and
+    plain u16 counts of other inputs, 3 rounds, outputs pre-filled with
+    garbage; every result equals the oracle."""
+    rng = np.random.default_rng(55)
+    streams = [torch.cuda.Stream() for _ in range(6)]
+    jobs = []
+    for i, s in enumerate(streams):
+        idb = (1, 2, 4, 1, 1, 2)[i]
+        k = (32, 17, 16, 9, 32, 5)[i]
+        n = int(rng.integers(1 << 20, (40 << 20) // idb))  # 8-bit ids: both sides of 32 MiB
+        ids = synth.categorical_ids(200 + i, n, synth.zipf_cdf(min(2 * k, 64)), DT[idb])
+        words = synth.uniform_bits(300 + i, int(rng.integers(1 << 20, 6 << 20)), 16)
+        wx = torch.from_numpy(words.view(np.uint8)).cuda()
+        jobs.append((s, k, _dev(ids, 0), oracle.onehot_counts(ids, k), wx, oracle.pospopcnt(words, 16)))
+    torch.cuda.synchronize()
+    for _ in range(3):
+        outs = []
+        for s, k, x, ref, wx, wref in jobs:
+            a = torch.randint(-2 ** 62, 2 ** 62, (k,), dtype=torch.int64, device="cuda")
+            b = torch.randint(-2 ** 62, 2 ** 62, (16,), dtype=torch.int64, device="cuda")
+            s.wait_stream(torch.cuda.current_stream())
+            ppc.pospopcnt_onehot_counts(x, k, counts=a, stream=s)
+            ppc.pospopcnt_u16(wx, counts=b, stream=s)
+            ppc.pospopcnt_onehot_counts(x, k, counts=a, stream=s)
+            outs.append((a, b))
+        torch.cuda.synchronize()
+        for (s, k, x, ref, wx, wref), (a, b) in zip(jobs, outs):
+            assert np.array_equal(a.cpu().numpy().view(np.uint64), ref), k
+            assert np.array_equal(b.cpu().numpy().view(np.uint64), wref)
