@@ -460,8 +460,7 @@ def run_plain(args, world, rank, local):
                 "traffic": profiled_traffic((f"onehot_k{onehot_k}" if words.itemsize == 1 else
                                              f"onehot{8 * words.itemsize}_k{onehot_k}") if onehot_k
                                             else f"{kname}_u{width}", nbytes),
-                "kernel": kernel_label + (f" (+ a {counts_bytes}-byte memset)" if onehot_k else
-                                          " (counts written by the last block, no memset)")}
+                "kernel": kernel_label + " (counts written by the last block, no memset)"}
     out = None
     if rank == 0:
         out = {
