@@ -39,6 +39,7 @@ sys.path.insert(0, ROOT)
 METRIC = "pospopcnt_u16 GB/s"
 UNIT = "GB/s"
 FALLBACK_HBM_GBS = 6800.0
+ALU_OPS_PER_ID_ONEHOT32 = 4.05  # one-hot count of 8-bit ids over 17..32 categories
 
 
 # ---------------------------------------------------------------------------
@@ -461,6 +462,25 @@ def run_plain(args, world, rank, local):
                                              f"onehot{8 * words.itemsize}_k{onehot_k}") if onehot_k
                                             else f"{kname}_u{width}", nbytes),
                 "kernel": kernel_label + " (counts written by the last block, no memset)"}
+    clk = clocks.summary()
+    if onehot_k > 16 and words.itemsize == 1:
+        # One 8-bit id per 32-bit register: the kernel is bound by its ALU
+        # pipe, not by HBM.  Its ALU operations per id, counted by ncu
+        # (sm__inst_executed_pipe_alu over the ids of a 2^27-id launch, less
+        # the per-CTA table set-up that a 2^31-id launch amortises): 4.05.
+        # The ALU pipe retires 16 thread-operations per cycle per SM
+        # sub-partition, 64 per SM.
+        sm_ghz = (clk.get("sm_mhz") or 2070.0) / 1e3
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        ids_per_s = words.size / (launch_ms * 1e-3) / 1e9
+        alu_peak = 64 * sms * sm_ghz / ALU_OPS_PER_ID_ONEHOT32
+        roofline = {"bound": "alu", "achieved": round(ids_per_s, 1), "peak": round(alu_peak, 1),
+                    "unit": "G ids/s", "frac": round(ids_per_s / alu_peak, 4),
+                    "peak_source": f"derived: 64 ALU operations per cycle per SM x {sms} SMs x {sm_ghz:.3f} GHz / "
+                                   f"{ALU_OPS_PER_ID_ONEHOT32} ALU operations per id",
+                    "traffic": roofline["traffic"], "kernel": roofline["kernel"],
+                    "hbm": {"achieved": roofline["achieved"], "peak": peak, "unit": "GB/s",
+                            "frac": roofline["frac"]}}
     out = None
     if rank == 0:
         out = {
@@ -484,7 +504,7 @@ def run_plain(args, world, rank, local):
             "roofline": roofline,
             "e2e": e2e,
             "gpu_launches": int(launches),
-            "clocks": clocks.summary(),
+            "clocks": clk,
             "checked": True,
             "checked_against": "oracle on the whole input (host threads), counts of the last timed step, "
                                "bit-exact",
