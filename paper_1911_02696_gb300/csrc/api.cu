@@ -815,6 +815,8 @@ int pospopcnt_autotune(int width, const void* d_in, size_t n, uint64_t* d_scratc
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  cudaStreamSynchronize(s);
+  ppc::release_slot(st->device, s);  // the accumulator the timed calls bound to the private stream
   cudaStreamDestroy(s);
   if (rc != POSPOPCNT_OK) return rc;
   float best_t = 1e30f;
