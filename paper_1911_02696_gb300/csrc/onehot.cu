@@ -8,8 +8,9 @@
 // bits (the smallest that holds k positions), 32/LW ids share one 32-bit
 // register -- and feeds those registers through the same carry-save circuit
 // and popc flush as the plain count.  Ids >= k encode to the empty word.
-// 32-bit ids are encoded by a clamped shift and a mask (circuit F_4).  8- and
-// 16-bit ids are encoded by lookups in a table in shared memory
+// 32-bit ids are encoded by a clamped shift and a mask (circuit F_4; F_5 for
+// one id per register).  8- and 16-bit ids are encoded by lookups in a table
+// in shared memory
 // (onehot_lut_kernel below 32 MiB, onehot_ring_kernel from 32 MiB, the
 // latter fed by bulk copies); for 8-bit ids and k <= 16 the bulk-copy kernel
 // looks up pairs of ids below 16, one lookup for two ids.
@@ -64,12 +65,24 @@ __device__ __forceinline__ uint32_t load_id(const uint8_t* p) {
   return *reinterpret_cast<const uint32_t*>(p);
 }
 
+// Trip of the shift-and-mask kernel: R registers through the circuit F_L,
+// U vectors per thread.  One id per register (LW = 32) takes 32 registers
+// (8 vectors of 32-bit ids in flight per thread) instead of 16: with 4
+// vectors per trip the loads in flight were too few to cover DRAM latency.
+template <int IDB, int LW>
+struct IdTrip {
+  static constexpr int IDS_PER_VEC = 16 / IDB;
+  static constexpr int IDS_PER_REG = 32 / LW;
+  static constexpr int REGS_PER_VEC = IDS_PER_VEC / IDS_PER_REG;
+  static constexpr int R = LW == 32 ? 32 : 16;
+  static constexpr int L = ilog2<R>::value;
+  static constexpr int U = R / REGS_PER_VEC;  // vectors per trip
+};
+
 template <int IDB, int LW, int NTHREADS>
 __global__ void __launch_bounds__(NTHREADS) onehot_kernel(OnehotArgs a) {
-  constexpr int IDS_PER_VEC = 16 / IDB;
-  constexpr int IDS_PER_REG = 32 / LW;
-  constexpr int REGS_PER_VEC = IDS_PER_VEC / IDS_PER_REG;
-  constexpr int U = 16 / REGS_PER_VEC;  // vectors per trip: 16 registers, circuit F_4
+  using TS = IdTrip<IDB, LW>;
+  constexpr int IDS_PER_REG = TS::IDS_PER_REG, REGS_PER_VEC = TS::REGS_PER_VEC, R = TS::R, L = TS::L, U = TS::U;
   const uint32_t k = a.k;
   // lane q of a register holds the one-hot bit of its id at bit q*LW + id;
   // the mask keeps bits q*LW .. q*LW + k - 1 (ids >= k, which could spill
@@ -78,13 +91,15 @@ __global__ void __launch_bounds__(NTHREADS) onehot_kernel(OnehotArgs a) {
   uint32_t lane_mask_q[IDS_PER_REG];
 #pragma unroll
   for (int q = 0; q < IDS_PER_REG; ++q) lane_mask_q[q] = km << (q * LW);
-  uint32_t B[4] = {0, 0, 0, 0};
+  uint32_t B[L];
+#pragma unroll
+  for (int l = 0; l < L; ++l) B[l] = 0;
   uint32_t top[LW];
 #pragma unroll
   for (int p = 0; p < LW; ++p) top[p] = 0;
   const uint64_t stride = uint64_t(gridDim.x) * NTHREADS;
   for (uint64_t v = uint64_t(blockIdx.x) * NTHREADS + threadIdx.x; v < a.nvec; v += U * stride) {
-    uint32_t d[16];
+    uint32_t d[R];
 #pragma unroll
     for (int i = 0; i < U; ++i) {
       const uint64_t idx = v + i * stride;
@@ -101,10 +116,10 @@ __global__ void __launch_bounds__(NTHREADS) onehot_kernel(OnehotArgs a) {
         d[i * REGS_PER_VEC + r] = live ? reg : 0u;
       }
     }
-    flush<LW>(top, Circuit<4>::run(d, B));
+    flush<LW>(top, Circuit<L>::run(d, B));
   }
   uint32_t c[LW];
-  finalize<LW, 4>(c, top, B);
+  finalize<LW, L>(c, top, B);
   if (blockIdx.x == 0) {  // head and tail ids (fewer than 16 each), one by one
     const unsigned t = threadIdx.x;
     if (t < a.head_ids) {
@@ -771,7 +786,7 @@ static int launch_onehot_ring(const DeviceState& st, OnehotArgs a, cudaStream_t 
 template <int IDB, int LW>
 static int launch_onehot(const DeviceState& st, OnehotArgs a, cudaStream_t stream) {
   constexpr int T = 256;
-  constexpr int U = 16 / ((16 / IDB) / (32 / LW));
+  constexpr int U = IdTrip<IDB, LW>::U;
   auto kern = onehot_kernel<IDB, LW, T>;
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, T, 0) != cudaSuccess || occ < 1) occ = 1;

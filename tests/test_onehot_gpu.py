@@ -172,3 +172,30 @@ def test_overwrite_on_streams_mixed_with_plain_counts():
         for (s, k, x, ref, wx, wref), (a, b) in zip(jobs, outs):
             assert np.array_equal(a.cpu().numpy().view(np.uint64), ref), k
             assert np.array_equal(b.cpu().numpy().view(np.uint64), wref)
+
+
+def _oracle_threads(ids, k, parts=16):
+    """The oracle over contiguous parts on host threads, results added (the
+    histogram of a concatenation is the sum of the parts' histograms)."""
+    from concurrent.futures import ThreadPoolExecutor
+    chunks = np.array_split(ids, parts)
+    with ThreadPoolExecutor(parts) as ex:
+        return np.sum(np.stack(list(ex.map(lambda c: oracle.onehot_counts(c, k), chunks))), axis=0,
+                      dtype=np.uint64)
+
+
+@pytest.mark.slow
+def test_four_gib_u8_ids():
+    """2^32 8-bit ids (4 GiB): all zero, so category 0 counts exactly 2^32
+    (past any 32-bit partial), and Zipf(1.1) over 32 categories against the
+    oracle; one-hot words of 17..32 categories go through the ALU-bound
+    bulk-copy kernel."""
+    zeros = np.zeros(1 << 32, dtype=np.uint8)
+    got = _run(zeros, 32)
+    assert got[0] == 1 << 32 and not got[1:].any()
+    del zeros
+    torch.cuda.empty_cache()
+    ids = synth.categorical_ids(7, 1 << 32, synth.zipf_cdf(32), np.uint8)
+    got = _run(ids, 32)
+    assert int(got.sum()) == 1 << 32
+    assert np.array_equal(got, _oracle_threads(ids, 32))
