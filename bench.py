@@ -807,9 +807,10 @@ def run_l2_states(args, world, rank, local):
 
 def run_ring_ab(args, world, rank, local):
     """Ring configurations of the bulk-copy kernel at 2 GiB, sustained: each
-    configuration counts the same buffer 1000 times back to back (CUDA events
-    around the 1000 calls, after 20 untimed ones), four rounds interleaved
-    across the configurations; GB/s per round and the median."""
+    of ten shapes counts the same buffer 300 times back to back (CUDA events
+    around the calls, after 10 untimed ones) at each width, three rounds
+    interleaved across the shapes, every result checked against the oracle;
+    GB/s per round and the median."""
     import torch
     import paper_1911_02696_gb300 as ppc
     import synth
@@ -817,33 +818,32 @@ def run_ring_ab(args, world, rank, local):
     dev = torch.device("cuda", local)
     ppc.pospopcnt_init(local)
     stream = torch.cuda.current_stream(dev)
-    x = torch.from_numpy(synth.uniform_bytes(rank, 2 << 30)).to(dev)
-    cands = {
-        8: [dict(kernel="tma", stages=4, chunk_bytes=32768), dict(kernel="tma", stages=2, chunk_bytes=98304, flags=1),
-            dict(kernel="tma", stages=3, chunk_bytes=65536)],
-        16: [dict(kernel="tma", stages=4, chunk_bytes=49152), dict(kernel="tma", stages=3, chunk_bytes=65536),
-             dict(kernel="tma", stages=3, chunk_bytes=65536, flags=1), dict(kernel="tma", stages=2, chunk_bytes=98304)],
-        32: [dict(kernel="tma", stages=3, chunk_bytes=65536), dict(kernel="tma", stages=4, chunk_bytes=49152),
-             dict(kernel="tma", stages=2, chunk_bytes=98304, flags=1), dict(kernel="tma", stages=4, chunk_bytes=32768)],
-        64: [dict(kernel="tma", stages=3, chunk_bytes=65536), dict(kernel="tma", stages=2, chunk_bytes=98304, flags=1),
-             dict(kernel="tma", stages=2, chunk_bytes=98304)],
-    }
+    host = synth.uniform_bytes(rank, 2 << 30)
+    x = torch.from_numpy(host).to(dev)
+    shapes = [(3, 49152, 0), (3, 49152, 1), (4, 49152, 0), (3, 65536, 0), (2, 98304, 0), (2, 98304, 1),
+              (4, 32768, 0), (5, 32768, 0), (2, 65536, 0), (3, 32768, 0)]
+    cands = {w: [dict(kernel="tma", stages=st, chunk_bytes=ch, flags=fl) for st, ch, fl in shapes]
+             for w in (8, 16, 32, 64)}
     rows = []
+    calls = 300
     for width, cl in cands.items():
         counts = torch.empty(width, dtype=torch.int64, device=dev)
+        ref = oracle_reference(host.view({8: np.uint8, 16: np.uint16, 32: np.uint32, 64: np.uint64}[width]), width)
         res = [[] for _ in cl]
-        for _ in range(4):
+        for _ in range(3):
             for i, cfg in enumerate(cl):
-                for _ in range(20):
+                for _ in range(10):
                     ppc.pospopcnt_count_config(width, cfg, x, counts=counts)
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 torch.cuda.synchronize()
                 a.record(stream)
-                for _ in range(1000):
+                for _ in range(calls):
                     ppc.pospopcnt_count_config(width, cfg, x, counts=counts)
                 b.record(stream)
                 torch.cuda.synchronize()
-                res[i].append(round(x.numel() * 1000 / (a.elapsed_time(b) * 1e-3) / 1e9, 1))
+                if not np.array_equal(counts.cpu().numpy().view(np.uint64), ref):
+                    raise CheckFailed(f"rank {rank}: ring {cfg} u{width} differs from the oracle")
+                res[i].append(round(x.numel() * calls / (a.elapsed_time(b) * 1e-3) / 1e9, 1))
         default = ppc.pospopcnt_get_config(width, x.numel() // (width // 8))
         for i, cfg in enumerate(cl):
             rows.append({"width": width, "config": cfg, "GBps_rounds": res[i],
@@ -852,9 +852,10 @@ def run_ring_ab(args, world, rank, local):
     if rank != 0:
         return None
     return {"metric": "pospopcnt GB/s by ring configuration (2 GiB, sustained)", "value": None, "unit": UNIT,
-            "n_gpus": world, "steps": 1000, "warmup": 20, "higher_is_better": True, "scaling": "weak",
+            "n_gpus": world, "steps": calls, "warmup": 10, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u8/u16/u32/u64", "data": "synthetic",
-            "config": {"workload": "2 GiB uniform bits, four interleaved rounds of 1000 calls"}, "rows": rows}
+            "config": {"workload": "2 GiB uniform bits, three interleaved rounds of 300 calls per shape"},
+            "rows": rows, "checked": True}
 
 
 def candidate_configs():

@@ -99,8 +99,8 @@ pospopcnt_config tuned_default(int width, int cls) {
     return c;
   }
   if (width == 8) {
-    if (cls >= 14) {  // 256 MiB and up: the ring, 4 x 32 KiB
-      c.kernel = POSPOPCNT_KERNEL_TMA, c.stages = 4, c.chunk_bytes = 32768;
+    if (cls >= 14) {  // 256 MiB and up: the ring, 4 x 32 KiB (5 x 32 KiB from 1 GiB)
+      c.kernel = POSPOPCNT_KERNEL_TMA, c.stages = cls >= 15 ? 5 : 4, c.chunk_bytes = 32768;
       return c;
     }
     c.threads = cls >= 13 ? 512 : 256;
