@@ -136,6 +136,34 @@ def test_full_20k_segments_one_hot():
     assert np.array_equal(got.sum(axis=1), lens.astype(np.uint64))
 
 
+@pytest.mark.slow
+def test_four_gib_segment_among_small_ones():
+    """One segment of 2^31 all-ones u16 words (4 GiB: every count 2^31, a
+    closed form) between small segments of uniform bits (the oracle), through
+    the batched form and its allocation-free variant."""
+    big = 1 << 31
+    small = synth.uniform_bits(12, 3000, 16)
+    words = np.empty(big + small.size, dtype=np.uint16)
+    words[:1000] = small[:1000]
+    words[1000: 1000 + big] = 0xFFFF
+    words[1000 + big:] = small[1000:]
+    off = np.array([0, 1, 1000, 1000 + big, 1000 + big + 7, words.size], dtype=np.int64)
+    _, x = _dev(words, 2)
+    d_off = torch.from_numpy(off).cuda()
+    ref = np.zeros((off.size - 1, 16), dtype=np.uint64)
+    for sgm in (0, 1, 3, 4):
+        ref[sgm] = oracle.pospopcnt(words[off[sgm]: off[sgm + 1]], 16)
+    ref[2] = big
+    got = ppc.pospopcnt_batched(x, d_off, 16).cpu().numpy().view(np.uint64)
+    assert np.array_equal(got, ref)
+    rows = torch.full((off.size - 1, 16), -1, dtype=torch.int64, device="cuda")
+    ppc.pospopcnt_batched_noalloc(x, d_off, 16, rows)
+    torch.cuda.synchronize()
+    assert np.array_equal(rows.cpu().numpy().view(np.uint64), ref)
+    del x
+    torch.cuda.empty_cache()
+
+
 def test_checked_form_valid_and_invalid_offsets():
     """pospopcnt_batched_checked counts valid offsets like pospopcnt_batched
     and turns offsets beyond the buffer or decreasing into an error status
