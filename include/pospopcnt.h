@@ -258,7 +258,7 @@ int pospopcnt_batched_checked(const void* d_in, size_t n_words, const int64_t* d
  * device address (cudaGetSymbolAddress, with that device current): make
  * that first call before any stream capture.  Every call on a device shares
  * the one array and clears all of it on its stream before launching, so
- * calls that overlap on the GPU (other streams, concurrent graph replays)
+ * calls that overlap on the GPU (calls on different streams, for instance)
  * race and give wrong counts: serialise them.  A wait that gave up is
  * reported by pospopcnt_check_device_error(stream), which allocates nothing
  * either, if it is called before the next call of this form on the device
