@@ -178,6 +178,17 @@ def dist_max(value: float, world: int, device=None) -> float:
     return float(t.item())
 
 
+def dist_all(flag: bool, world: int, device=None) -> bool:
+    """True on every rank iff `flag` is true on every rank."""
+    if world <= 1:
+        return flag
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([1 if flag else 0], dtype=torch.int32, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MIN)
+    return bool(t.item())
+
+
 def dist_barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -384,11 +395,14 @@ def run_plain(args, world, rank, local):
     launches = ppc.pospopcnt_launch_count() - launches0
     time.sleep(0.3)
     clocks.stop()
-    # the counts of the last timed step against the oracle on the whole input
+    # the counts of the last timed step against the oracle on the whole input;
+    # every rank learns every rank's verdict, so all stop together on a mismatch
     got = counts.cpu().numpy().view(np.uint64).copy()
     ref = oracle_reference(words, width, onehot_k)
-    if not np.array_equal(got, ref):
-        raise CheckFailed(f"rank {rank}: timed counts {got.tolist()} differ from the oracle's {ref.tolist()}")
+    ok = bool(np.array_equal(got, ref))
+    if not dist_all(ok, world, device=dev if world > 1 else None):
+        raise CheckFailed(f"rank {rank}: timed counts {got.tolist()} vs the oracle's {ref.tolist()}"
+                          if not ok else f"rank {rank}: another rank's timed counts differ from the oracle's")
     total_ms = ev[0].elapsed_time(ev[-1])
     per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     max_ms = dist_max(total_ms, world, device=dev if world > 1 else None)

@@ -1,7 +1,7 @@
 """bench.py's multi-rank harness on CPU with the gloo backend (world size
 2): the slowest rank's time is what every rank reports, the whole-job value
-counts every rank's bytes, and under torchrun only rank 0 prints its JSON
-line.  The data path itself has no collective (each rank counts its own
+counts every rank's bytes, a result check failing on one rank fails on every
+rank, and under torchrun only rank 0 prints its JSON line.  The data path itself has no collective (each rank counts its own
 input), so nothing else crosses ranks."""
 import json
 import os
@@ -32,7 +32,10 @@ def _worker(rank, world, port, q):
     slowest = bench.dist_max(10.0 + rank, world)
     bench.dist_barrier(world)
     value = bench.whole_job_throughput(1 << 31, 100, world, slowest * 1000)
-    q.put((rank, slowest, value))
+    # a result check that fails on one rank fails on every rank
+    all_ok = bench.dist_all(True, world)
+    one_bad = bench.dist_all(rank != 1, world)
+    q.put((rank, slowest, value, all_ok, one_bad))
     dist.destroy_process_group()
 
 
@@ -48,9 +51,10 @@ def test_gloo_max_and_whole_job_value():
         p.join(120)
         assert p.exitcode == 0
     got = sorted(q.get(timeout=10) for _ in range(2))
-    for rank, slowest, value in got:
+    for rank, slowest, value, all_ok, one_bad in got:
         assert slowest == 11.0  # the max over ranks, on every rank
         assert value == pytest.approx(2 * 100 * (1 << 31) / 11.0 / 1e9)
+        assert all_ok is True and one_bad is False
 
 
 def test_torchrun_reference_arm_prints_once():
