@@ -199,3 +199,18 @@ def test_four_gib_u8_ids():
     got = _run(ids, 32)
     assert int(got.sum()) == 1 << 32
     assert np.array_equal(got, _oracle_threads(ids, 32))
+
+
+@pytest.mark.slow
+def test_full_u16_and_u32_ids():
+    """The bench's 16- and 32-bit-id workloads at full size (2 GiB: 2^30 u16
+    ids, 2^29 u32 ids), Zipf(1.1) over 16 and over 32 categories, against
+    the oracle."""
+    for idb, n in ((2, 1 << 30), (4, 1 << 29)):
+        for k in (16, 32):
+            ids = synth.categorical_ids(60 + k, n, synth.zipf_cdf(k), DT[idb])
+            got = _run(ids, k)
+            assert int(got.sum()) == n
+            assert np.array_equal(got, _oracle_threads(ids, k)), (idb, k)
+            del ids
+            torch.cuda.empty_cache()
