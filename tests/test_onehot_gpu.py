@@ -214,3 +214,34 @@ def test_full_u16_and_u32_ids():
             assert np.array_equal(got, _oracle_threads(ids, k)), (idb, k)
             del ids
             torch.cuda.empty_cache()
+
+
+def test_graph_capture_of_onehot_and_popcount():
+    """One-hot and popcount calls captured into CUDA graphs (they zero their
+    outputs with a memset while the stream is captured, so a graph may be
+    replayed on any stream): replays on two other streams, outputs reset to
+    garbage in between, equal the oracle."""
+    ids = synth.categorical_ids(70, (9 << 20) + 1, synth.zipf_cdf(32), np.uint8)
+    x = _dev(ids, 1)
+    b = synth.uniform_bytes(71, (40 << 20) + 3)
+    xb = torch.from_numpy(b).cuda()
+    h = torch.empty(32, dtype=torch.int64, device="cuda")
+    pc = torch.empty(1, dtype=torch.int64, device="cuda")
+    ppc.pospopcnt_onehot_counts(x, 32, counts=h)
+    ppc.pospopcnt_popcount(xb, count=pc)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        ppc.pospopcnt_onehot_counts(x, 32, counts=h)
+        ppc.pospopcnt_popcount(xb, count=pc)
+    ref_h = oracle.onehot_counts(ids, 32)
+    ref_pc = int(oracle.pospopcnt(b, 8).sum())
+    for s in (torch.cuda.Stream(), torch.cuda.Stream()):
+        h.fill_(-3)
+        pc.fill_(-3)
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            g.replay()
+        s.synchronize()
+        assert np.array_equal(h.cpu().numpy().view(np.uint64), ref_h)
+        assert int(pc.cpu()[0]) == ref_pc
