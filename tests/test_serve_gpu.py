@@ -161,3 +161,29 @@ def test_mixed_routes_same_results(pool):
     assert np.array_equal(mixed, _oracle_rows(host, tr))
     assert np.array_equal(mixed, _solo_rows(dev, tr))
     assert st["completed"] == tr["t_arrival"].size
+
+
+def test_high_rate_batches_form_and_results_match(pool):
+    """Arrivals faster than one launch per request (400k req/s of payloads up
+    to 64 KiB for 0.25 s) with 16 slots in both modes: continuous batching
+    puts several jobs in a launch, and every request's counts are the same in
+    the batched mix, in per-request mode (each job counted alone) and in the
+    oracle."""
+    host, dev = pool
+    tr = _trace(9, rate=400000, duration=0.25, max_bytes=64 << 10)
+    res = {}
+    for per_request in (False, True):
+        srv = ppc.pospopcnt_server_create(0, max_inflight=16, per_request=per_request,
+                                          max_batch_jobs=1 if per_request else 240)
+        try:
+            lat, counts, status = _run(srv, dev, tr)
+            st = ppc.pospopcnt_server_get_stats(srv)
+        finally:
+            ppc.pospopcnt_server_destroy(srv)
+        assert np.all(status == 0)
+        assert st["completed"] == tr["t_arrival"].size
+        res[per_request] = (counts, st)
+    batched, st_b = res[False]
+    assert st_b["max_batch"] > 1 and st_b["batches"] < st_b["completed"]
+    assert np.array_equal(batched, res[True][0])
+    assert np.array_equal(batched, _oracle_rows(host, tr))
