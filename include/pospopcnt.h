@@ -287,7 +287,8 @@ int pospopcnt_plain_segments(const void* d_in, const int64_t* h_offsets, size_t 
  * that job complete as soon as its own last piece is counted, so a job never
  * waits for the rest of its batch.
  * Jobs of at least large_job_bytes are launched on their own with the
- * tuned plain count (added into a row kept at zero, then published through
+ * tuned plain count (the bulk-copy ring from 64 MiB, as served payloads are
+ * read-only; added into a row kept at zero, then published through
  * the same flag by a one-warp kernel).  per_request = 1 launches every job
  * that way (one plain count per job), the comparison the batched form is
  * measured against. */
