@@ -39,7 +39,7 @@ sys.path.insert(0, ROOT)
 METRIC = "pospopcnt_u16 GB/s"
 UNIT = "GB/s"
 FALLBACK_HBM_GBS = 6800.0
-ALU_OPS_PER_ID_ONEHOT32 = 4.05  # one-hot count of 8-bit ids over 17..32 categories
+ALU_OPS_PER_ID_ONEHOT32 = 3.28  # one-hot count of 8-bit ids over 17..32 categories
 
 
 # ---------------------------------------------------------------------------
@@ -486,9 +486,10 @@ def run_plain(args, world, rank, local):
     if onehot_k > 16 and words.itemsize == 1:
         # One 8-bit id per 32-bit register: the kernel is bound by its ALU
         # pipe, not by HBM.  Its ALU operations per id, counted by ncu
-        # (sm__inst_executed_pipe_alu over the ids of a 2^27-id launch, less
-        # the per-CTA table set-up that a 2^31-id launch amortises): 4.05.
-        # The ALU pipe retires 16 thread-operations per cycle per SM
+        # (smsp__inst_executed_pipe_alu of a 2^27-id and a 2^30-id launch):
+        # 3.26 per id between the two sizes, plus the per-CTA work (table
+        # set-up, ring ramp, reduction) spread over a 2^31-id launch, 0.02:
+        # 3.28.  The ALU pipe retires 16 thread-operations per cycle per SM
         # sub-partition, 64 per SM.
         sm_ghz = (clk.get("sm_mhz") or 2070.0) / 1e3
         sms = torch.cuda.get_device_properties(dev).multi_processor_count

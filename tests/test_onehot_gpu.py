@@ -109,6 +109,25 @@ def test_u8_pairs_and_mixed_trips(k):
     assert int(got.sum()) == int(np.sum(mixed < k))
 
 
+@pytest.mark.parametrize("k", [20, 32])
+def test_ring_warp_flush_one_id_per_register(k):
+    """17..32 categories on the bulk-copy path: each warp transposes its
+    lanes' carry registers so that lane p collects position p.  Ids that are
+    a function of the 16-byte vector's index (so of the lane that counts
+    them; ids 20..31 count nothing at k = 20), and one constant id per input
+    at the edges of the transpose's 16-, 8-, 4-, 2- and 1-column blocks,
+    each with a partial last ring chunk."""
+    n = (40 << 20) + 4099
+    v = np.arange(n, dtype=np.int64) // 16
+    ids = ((v * 7 + (v >> 5)) % 32).astype(np.uint8)
+    assert np.array_equal(_run(ids, k, 1), oracle.onehot_counts(ids, k))
+    for c in (0, 1, 2, 3, 4, 7, 8, 15, 16, 23, 24, 31):
+        ids = np.full(n, c, dtype=np.uint8)
+        got = _run(ids, k)
+        assert np.array_equal(got, oracle.onehot_counts(ids, k)), c
+        assert int(got.sum()) == (n if c < k else 0), c
+
+
 @pytest.mark.parametrize("k", [1, 8, 16, 32])
 def test_u16_ids_with_high_bytes(k):
     """16-bit ids whose low byte is a valid category but whose high byte is
