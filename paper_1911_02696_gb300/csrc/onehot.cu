@@ -432,20 +432,24 @@ __device__ __forceinline__ uint32_t warp_column_counts(uint32_t x) {
   return static_cast<uint32_t>(__popc(x));
 }
 
-// The counter of PairedCounts for one id per register (LW = 32), with the
-// flush done by the warp: the carry out of the last level (weight
-// 2^(N+D)) goes through warp_column_counts, so lane p keeps the warp's count
-// of position p in one register instead of every lane keeping 32 (6.8 %
-// faster on 2 GiB of ids: fewer flush instructions, 31 registers free).
-// finish() returns the warp's count of position `lane`.  Every lane of a
-// warp must add the same number of trips (the bulk-copy kernel's trips are
-// the same for the whole CTA), as the flush is a warp-wide exchange.
-template <int N, int D>
+// The counter of PairedCounts with the flush done by the warp: the carry
+// out of the last level (weight 2^(N+D)) goes through warp_column_counts,
+// so lane q keeps the warp's count of register bit q in one register
+// instead of every lane keeping LW counters; bits q, q + LW, ... are the
+// same category and are summed once, at the end (on 2 GiB of 8-bit ids:
+// 4809 -> 5137 GB/s for 17-32 categories, 6855 -> 7039 for 9-16, 7097 ->
+// 7133 for up to 8, against the per-thread flush).  finish() returns the
+// warp's counts in the layout of warp_reduce_positions (lane i: position
+// i >> (5 - log2 LW)).  Every lane of a warp must add the same number of
+// trips (the bulk-copy kernel's trips are the same for the whole CTA), as
+// the flush is a warp-wide exchange.
+template <int LW, int N, int D>
 struct ColumnCounts {
   uint32_t B[N + D];  // B[l] at weight 2^l
   uint32_t pend[D];   // pend[j]: unpaired register of weight 2^(N+j)
   uint32_t trips = 0;
-  uint32_t top = 0;   // lane p: the warp's carries at position p, units of 2^(N+D)
+  uint32_t top = 0;   // lane q: the warp's carries at bit q, units of 2^(N+D)
+  uint32_t ones = 0;  // lane q: single words added at bit q (add_word)
   __device__ __forceinline__ ColumnCounts() {
 #pragma unroll
     for (int l = 0; l < N + D; ++l) B[l] = 0;
@@ -472,12 +476,20 @@ struct ColumnCounts {
     carry_into<0>(t, __ffs(~trips) - 1);
     ++trips;
   }
+  // One encoded word of weight 1 (every lane of the warp calls it).
+  __device__ __forceinline__ void add_word(uint32_t w) { ones += warp_column_counts(w); }
   __device__ __forceinline__ uint32_t finish() const {
-    uint32_t v = top << (N + D);
+    uint32_t v = (top << (N + D)) + ones;
 #pragma unroll
     for (int l = 0; l < N + D; ++l) v += warp_column_counts(B[l]) << l;
 #pragma unroll
     for (int j = 0; j < D; ++j) v += warp_column_counts(pend[j]) << (N + j);
+    if constexpr (LW < 32) {
+      constexpr int SH = 5 - ilog2<LW>::value;
+#pragma unroll
+      for (int s = 16; s >= LW; s >>= 1) v += __shfl_down_sync(FULL_MASK, v, s);  // lane p < LW: category p
+      v = __shfl_sync(FULL_MASK, v, (threadIdx.x & 31u) >> SH);
+    }
     return v;
   }
 };
@@ -686,15 +698,10 @@ struct RingTrip<32, 1> {
   static constexpr int U = 4;
 };
 
-// The ring kernel's per-thread counter: one id per register (LW = 32) keeps
-// its flushed counts per warp (ColumnCounts), the packed widths per thread.
+// The ring kernel's counter: the flush done by the warp, at every width.
 template <int LW, int IDB>
 struct RingAccT {
-  using type = PairedCounts<LW, RingTrip<LW, IDB>::N, ring_depth<LW>::value>;
-};
-template <int IDB>
-struct RingAccT<32, IDB> {
-  using type = ColumnCounts<RingTrip<32, IDB>::N, ring_depth<32>::value>;
+  using type = ColumnCounts<LW, RingTrip<LW, IDB>::N, ring_depth<LW>::value>;
 };
 template <int LW, int IDB>
 using RingAcc = typename RingAccT<LW, IDB>::type;
@@ -730,6 +737,18 @@ __device__ __forceinline__ void ring_trip(const uint4* sv, uint32_t base, uint32
     for (int j = 0; j < U; ++j) encode_vec<LW, IDB, IMM>(d + j * REGS_PER_VEC, y[j], t, lanebase, one);
   }
   acc.add_trip(d, one);
+}
+
+// Block 0's consumer threads 0..15 and 32..47 count the head and tail ids
+// (fewer than 16 each, outside the 16-byte vectors): the encoded word of
+// the thread's id, or 0.
+template <int LW, int IDB>
+__device__ __forceinline__ uint32_t head_tail_word(const OnehotArgs& a) {
+  const unsigned t = threadIdx.x;
+  uint32_t id = 0xFFFFFFFFu;
+  if (t < a.head_ids) id = load_id<IDB>(a.head + t * IDB);
+  if (t >= 32 && t - 32 < a.tail_ids) id = load_id<IDB>(a.tail + (t - 32) * IDB);
+  return id < a.k ? 1u << id : 0u;
 }
 
 // The consumer warps' loop over this CTA's chunks; returns the chunks it
@@ -809,10 +828,7 @@ __global__ void __launch_bounds__(RING_THREADS, 1) onehot_ring_kernel(OnehotArgs
   }
   __syncthreads();
 
-  uint32_t c[LW];
-#pragma unroll
-  for (int p = 0; p < LW; ++p) c[p] = 0;
-  uint32_t vsum = 0;  // LW = 32: the warp's count of position `lane`
+  uint32_t vsum = 0;  // the warp's counts, lane i: position i >> (5 - log2 LW)
   if (warp == RING_CWARPS) {
     if (lane == 0) {  // producer: one lane issues every copy
       uint32_t i = 0;
@@ -845,10 +861,8 @@ __global__ void __launch_bounds__(RING_THREADS, 1) onehot_ring_kernel(OnehotArgs
                                                     lanebase, acc)
             : ring_consume<LW, IDB, 0>(a, ring, ctl, my_chunks, LutRef<0>{base}, lanebase, acc);
     if (lane == 0) ctl->consumed[warp] = done;
-    if constexpr (LW == 32)
-      vsum = acc.finish();
-    else
-      acc.finish(c);
+    if (blockIdx.x == 0) acc.add_word(head_tail_word<LW, IDB>(a));  // every lane of the warp
+    vsum = acc.finish();
   }
   __syncthreads();
   // After an abort, wait (bounded) for copies still in flight before the
@@ -863,27 +877,8 @@ __global__ void __launch_bounds__(RING_THREADS, 1) onehot_ring_kernel(OnehotArgs
       }
     }
   }
-  if (blockIdx.x == 0) {  // head and tail ids (fewer than 16 each), one by one
-    const unsigned t = threadIdx.x;
-    uint32_t word = 0;
-    if (t < a.head_ids) {
-      const uint32_t id = load_id<IDB>(a.head + t * IDB);
-      word = id < a.k ? 1u << id : 0u;
-    }
-    if (t >= 32 && t - 32 < a.tail_ids) {
-      const uint32_t id = load_id<IDB>(a.tail + (t - 32) * IDB);
-      word = id < a.k ? 1u << id : 0u;
-    }
-    if constexpr (LW == 32)
-      vsum += warp_column_counts(word);  // every lane of every warp of block 0
-    else
-      count_word<LW>(c, word);
-  }
   // block reduction in the table's memory; the producer warp holds no counts
-  if constexpr (LW == 32)
-    reduce_warp_sums_in<LW, RING_CWARPS>(reinterpret_cast<uint32_t*>(lut), vsum, a, &ctl->last);
-  else
-    reduce_counts_in<LW, RING_CWARPS>(reinterpret_cast<uint32_t*>(lut), c, a, &ctl->last);
+  reduce_warp_sums_in<LW, RING_CWARPS>(reinterpret_cast<uint32_t*>(lut), vsum, a, &ctl->last);
 }
 
 template <int LW, int IDB>
