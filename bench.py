@@ -471,11 +471,9 @@ def run_plain(args, world, rank, local):
         cfg, kname = {"kernel": "onehot", "k": onehot_k}, "onehot"
         lw = 8 if onehot_k <= 8 else 16 if onehot_k <= 16 else 32
         idb = words.itemsize
-        if idb <= 2:
-            kernel_label = (f"onehot_ring_kernel<{lw}, {idb}>" if nbytes >= (32 << 20) else
-                            f"onehot_lut_kernel<{lw}, {idb}, 256>") + f" ({8 * idb}-bit ids, k = {onehot_k})"
-        else:
-            kernel_label = f"onehot_kernel<{idb}, {lw}, 256> ({8 * idb}-bit ids, k = {onehot_k})"
+        kernel_label = (f"onehot_ring_kernel<{lw}, {idb}>" if nbytes >= (32 << 20) else
+                        f"onehot_lut_kernel<{lw}, {idb}, 256>" if idb <= 2 else
+                        f"onehot_kernel<{idb}, {lw}, 256>") + f" ({8 * idb}-bit ids, k = {onehot_k})"
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_source": f"{peak_src} (copy bandwidth)",
                 "traffic": profiled_traffic((f"onehot_k{onehot_k}" if words.itemsize == 1 else

@@ -8,11 +8,11 @@
 // bits (the smallest that holds k positions), 32/LW ids share one 32-bit
 // register -- and feeds those registers through the same carry-save circuit
 // and popc flush as the plain count.  Ids >= k encode to the empty word.
-// 32-bit ids are encoded by a clamped shift and a mask (circuit F_4; F_5 for
-// one id per register).  8- and 16-bit ids are encoded by lookups in a table
-// in shared memory
-// (onehot_lut_kernel below 32 MiB, onehot_ring_kernel from 32 MiB, the
-// latter fed by bulk copies); for 8-bit ids and k <= 16 the bulk-copy kernel
+// 32-bit ids are encoded by a clamped shift and a mask (onehot_kernel below
+// 32 MiB: circuit F_4, F_5 for one id per register).  8- and 16-bit ids are
+// encoded by lookups in a table in shared memory (onehot_lut_kernel below
+// 32 MiB).  From 32 MiB every id width goes through onehot_ring_kernel, fed
+// by bulk copies, with the same two encodings; for 8-bit ids and k <= 16 it
 // looks up pairs of ids below 16, one lookup for two ids.
 #include <cuda_runtime.h>
 
@@ -310,6 +310,22 @@ __device__ __forceinline__ void encode_vec_shift(uint32_t* d, const uint4& x, ui
       const uint32_t id = __byte_perm(w[j / 4], 0u, 0x4440u | unsigned(j % 4));
       reg |= shl_clamped(1u << (q * LW), id) & (km << (q * LW));
     }
+    d[r] = reg;
+  }
+}
+
+// 32-bit ids (the bulk-copy kernel): each id by a clamped shift and a mask,
+// 32/LW ids per register.  km = (1 << k) - 1; an id of 32 or more shifts
+// its bit out of the register, one in [k, 32) is masked off.
+template <int LW>
+__device__ __forceinline__ void encode_vec_ids32(uint32_t* d, const uint4& x, uint32_t km) {
+  constexpr int IPR = 32 / LW;  // ids per register
+  const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+  for (int r = 0; r < 4 / IPR; ++r) {
+    uint32_t reg = 0;
+#pragma unroll
+    for (int q = 0; q < IPR; ++q) reg |= shl_clamped(1u << (q * LW), w[r * IPR + q]) & (km << (q * LW));
     d[r] = reg;
   }
 }
@@ -732,6 +748,9 @@ __device__ __forceinline__ void ring_trip(const uint4* sv, uint32_t base, uint32
 #pragma unroll
       for (int j = 0; j < U; ++j) encode_vec_shift<LW>(d + j * REGS_PER_VEC, y[j], km);
     }
+  } else if constexpr (IDB == 4) {
+#pragma unroll
+    for (int j = 0; j < U; ++j) encode_vec_ids32<LW>(d + j * REGS_PER_VEC, y[j], km);
   } else {
 #pragma unroll
     for (int j = 0; j < U; ++j) encode_vec<LW, IDB, IMM>(d + j * REGS_PER_VEC, y[j], t, lanebase, one);
@@ -820,11 +839,13 @@ __global__ void __launch_bounds__(RING_THREADS, 1) onehot_ring_kernel(OnehotArgs
     ctl->abort = 0;
     mbar_fence_init();
   }
-  for (uint32_t e = warp; e < 256u; e += RING_CWARPS + 1) {
-    const bool pairs = RingPairs<LW, IDB>::value;
-    *reinterpret_cast<uint32_t*>(lut + e * LUT_ROW + lane * 4u) = pairs ? pair_lo<LW>(e, a.k) : lut_lo<LW>(e, a.k);
-    *reinterpret_cast<uint32_t*>(lut + e * LUT_ROW + 128u + lane * 4u) =
-        pairs ? pair_hi<LW>(e, a.k) : lut_hi<LW>(e, a.k);
+  if constexpr (IDB < 4) {  // 32-bit ids need no table
+    for (uint32_t e = warp; e < 256u; e += RING_CWARPS + 1) {
+      const bool pairs = RingPairs<LW, IDB>::value;
+      *reinterpret_cast<uint32_t*>(lut + e * LUT_ROW + lane * 4u) = pairs ? pair_lo<LW>(e, a.k) : lut_lo<LW>(e, a.k);
+      *reinterpret_cast<uint32_t*>(lut + e * LUT_ROW + 128u + lane * 4u) =
+          pairs ? pair_hi<LW>(e, a.k) : lut_hi<LW>(e, a.k);
+    }
   }
   __syncthreads();
 
@@ -927,12 +948,12 @@ static int launch_onehot(const DeviceState& st, OnehotArgs a, cudaStream_t strea
 
 template <int IDB>
 static int launch_onehot_idb(const DeviceState& st, const OnehotArgs& a, cudaStream_t stream) {
+  if (a.nvec * 16 >= RING_MIN_BYTES) {  // enough chunks to give every SM several
+    if (a.k <= 8) return launch_onehot_ring<8, IDB>(st, a, stream);
+    if (a.k <= 16) return launch_onehot_ring<16, IDB>(st, a, stream);
+    return launch_onehot_ring<32, IDB>(st, a, stream);
+  }
   if constexpr (IDB <= 2) {
-    if (a.nvec * 16 >= RING_MIN_BYTES) {  // enough chunks to give every SM several
-      if (a.k <= 8) return launch_onehot_ring<8, IDB>(st, a, stream);
-      if (a.k <= 16) return launch_onehot_ring<16, IDB>(st, a, stream);
-      return launch_onehot_ring<32, IDB>(st, a, stream);
-    }
     if (a.k <= 8) return launch_onehot_lut<8, IDB>(st, a, stream);
     if (a.k <= 16) return launch_onehot_lut<16, IDB>(st, a, stream);
     return launch_onehot_lut<32, IDB>(st, a, stream);

@@ -2,7 +2,8 @@
 encodes each id and then counts positions, §1): every id width, k on both
 sides of the 8/16/32-bit lane boundaries, ids >= k present, every small
 length at every aligned start, ragged large sizes, skewed ids, both 8-bit-id
-kernels (register loads below 32 MiB, bulk-copy ring above), 2 GiB."""
+kernels (register loads below 32 MiB, bulk-copy ring above; 32-bit ids
+too), 2 GiB."""
 import numpy as np
 import pytest
 
@@ -70,18 +71,22 @@ def test_u8_every_id_value(k):
         assert np.array_equal(_run(ids, k, int(rng.integers(0, 16))), oracle.onehot_counts(ids, k)), n
 
 
-@pytest.mark.parametrize("idb", [1, 2])
+@pytest.mark.parametrize("idb", [1, 2, 4])
 @pytest.mark.parametrize("k", [3, 8, 16, 17, 32])
 def test_bulk_copy_sizes(idb, k):
-    """8- and 16-bit ids from 32 MiB up go through bulk copies into a
-    shared-memory ring: the exact threshold, a ragged chunk count, a partial
-    last chunk at an odd start, ids over the whole id range and skewed ids."""
+    """Ids from 32 MiB up go through bulk copies into a shared-memory ring
+    (8- and 16-bit ids encoded by table lookups, 32-bit ids by shift and
+    mask): the exact threshold, a ragged chunk count, a partial last chunk
+    at an odd start, ids over the whole id range (for 32-bit ids, also ids
+    below 64, most of them counted) and skewed ids."""
     rng = np.random.default_rng(100 + k + 1000 * idb)
-    top = 256 if idb == 1 else 65536
+    top = {1: 256, 2: 65536, 4: 1 << 32}[idb]
     sizes = [(32 << 20, 0), ((32 << 20) - 16, 0), (152 * 32768 * 7 + 16 * 100 + 3, 5), ((40 << 20) + 17, 3)]
     for nbytes, off in sizes:
         n = nbytes // idb
         ids = rng.integers(0, top, size=n).astype(DT[idb])
+        if idb == 4 and nbytes % 2:
+            ids = rng.integers(0, 64, size=n).astype(DT[idb])
         assert np.array_equal(_run(ids, k, off - off % idb), oracle.onehot_counts(ids, k)), (n, off)
     ids = synth.categorical_ids(k, ((48 << 20) + 9) // idb, synth.zipf_cdf(min(2 * k, 64)), DT[idb])
     assert np.array_equal(_run(ids, k, idb), oracle.onehot_counts(ids, k))
@@ -140,6 +145,23 @@ def test_u16_ids_with_high_bytes(k):
         valid = rng.integers(0, k, size=n).astype(np.uint16)
         ids = np.where(rng.random(n) < 0.5, valid, decoys[rng.integers(0, decoys.size, size=n)]).astype(np.uint16)
         got = _run(ids, k, 2 * int(rng.integers(0, 8)))
+        assert np.array_equal(got, oracle.onehot_counts(ids, k)), n
+        assert int(got.sum()) == int(np.sum(ids < k))
+
+
+@pytest.mark.parametrize("k", [1, 8, 9, 16, 17, 32])
+def test_u32_ids_decoys(k):
+    """32-bit ids are encoded by a clamped shift: ids of 32 and more (low
+    bits a valid category, high bits set, 2^31, 0xFFFFFFFF) must count
+    nowhere, mixed with valid ids, below 32 MiB (register loads) and above
+    (bulk-copy ring)."""
+    rng = np.random.default_rng(11 + k)
+    decoys = np.array([32 + j for j in range(32)] + [0x100 + j for j in range(32)] + [0x10000 + j for j in range(32)] +
+                      [0xFFFFFFE0 + j for j in range(32)] + [1 << 31, 0xFFFFFFFF], dtype=np.uint32)
+    for n in (1000, (3 << 20) + 5, (10 << 20) + 3):
+        valid = rng.integers(0, k, size=n).astype(np.uint32)
+        ids = np.where(rng.random(n) < 0.5, valid, decoys[rng.integers(0, decoys.size, size=n)]).astype(np.uint32)
+        got = _run(ids, k, 4 * int(rng.integers(0, 4)))
         assert np.array_equal(got, oracle.onehot_counts(ids, k)), n
         assert int(got.sum()) == int(np.sum(ids < k))
 
