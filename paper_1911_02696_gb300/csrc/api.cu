@@ -181,6 +181,35 @@ int cuda_fail(cudaError_t e) {
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+namespace {
+struct OccupancyEntry {
+  const void* func;
+  int device, threads;
+  size_t smem;
+  int blocks;
+};
+constexpr int OCCUPANCY_ENTRIES = 512;  // kernels x devices x launch shapes the library can use
+std::mutex g_occ_mu;
+OccupancyEntry g_occ[OCCUPANCY_ENTRIES];
+int g_occ_used = 0;
+}  // namespace
+
+int resident_blocks(const void* func, int device, int threads, size_t smem) {
+  {
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    for (int i = 0; i < g_occ_used; ++i) {
+      const OccupancyEntry& e = g_occ[i];
+      if (e.func == func && e.device == device && e.threads == threads && e.smem == smem) return e.blocks;
+    }
+  }
+  int blocks = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, func, threads, smem) != cudaSuccess || blocks < 1)
+    return 1;  // not remembered: a failed query is asked again next time
+  std::lock_guard<std::mutex> lk(g_occ_mu);
+  if (g_occ_used < OCCUPANCY_ENTRIES) g_occ[g_occ_used++] = OccupancyEntry{func, device, threads, smem, blocks};
+  return blocks;
+}
+
 cudaError_t device_alloc(void** p, size_t bytes) {
   const cudaError_t e = cudaMalloc(p, bytes);
   if (e == cudaSuccess) g_device_bytes.fetch_add(bytes, std::memory_order_relaxed);

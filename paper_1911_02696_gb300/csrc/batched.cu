@@ -264,9 +264,7 @@ static int launch_batched_ks(const DeviceState& st, const BatchedArgs& a, cudaSt
   static_assert(smem <= BT_RING_MAX_SMEM, "ring larger than a launch may ask for");
   if (const cudaError_t e = ensure_dynamic_smem<batched_kernel<K, STAGES, VPL>>(st.device, int(smem)))
     return cuda_fail(e);
-  int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, BT_THREADS, smem) != cudaSuccess || occ < 1)
-    occ = 1;
+  const int occ = resident_blocks(reinterpret_cast<const void*>(kern), st.device, BT_THREADS, smem);
   const int bps = blocks_per_sm > 0 && blocks_per_sm < occ ? blocks_per_sm : occ;
   const unsigned grid = unsigned(st.sms) * unsigned(bps);
   kern<<<grid, BT_THREADS, smem, stream>>>(a);

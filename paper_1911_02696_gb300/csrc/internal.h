@@ -45,6 +45,13 @@ int cuda_fail(cudaError_t e);
 // Counts one kernel launch.
 void note_launch();
 
+// Resident blocks per SM of kernel `func` with `threads` threads and `smem`
+// bytes of dynamic shared memory on `device` (the current device), at least
+// 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor, asked once per kernel,
+// device, block size and shared-memory size and then remembered, since the
+// answer cannot change within a process.
+int resident_blocks(const void* func, int device, int threads, size_t smem);
+
 // cudaMalloc / cudaFree of device memory the library owns; the bytes held
 // are counted for pospopcnt_device_bytes_allocated.
 cudaError_t device_alloc(void** p, size_t bytes);

@@ -649,8 +649,7 @@ static int launch_onehot_lut(const DeviceState& st, OnehotArgs a, cudaStream_t s
   auto kern = onehot_lut_kernel<LW, IDB, T>;
   if (const cudaError_t e = ensure_dynamic_smem<onehot_lut_kernel<LW, IDB, T>>(st.device, LUT_BYTES))
     return cuda_fail(e);
-  int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, T, LUT_BYTES) != cudaSuccess || occ < 1) occ = 1;
+  const int occ = resident_blocks(reinterpret_cast<const void*>(kern), st.device, T, LUT_BYTES);
   const uint64_t cap = uint64_t(st.sms) * uint64_t(occ);
   const uint64_t need = (a.nvec + uint64_t(U) * T - 1) / (uint64_t(U) * T);
   uint64_t grid = std::max<uint64_t>(1, std::min(cap, need));
@@ -928,8 +927,7 @@ static int launch_onehot(const DeviceState& st, OnehotArgs a, cudaStream_t strea
   constexpr int T = 256;
   constexpr int U = IdTrip<IDB, LW>::U;
   auto kern = onehot_kernel<IDB, LW, T>;
-  int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, T, 0) != cudaSuccess || occ < 1) occ = 1;
+  const int occ = resident_blocks(reinterpret_cast<const void*>(kern), st.device, T, 0);
   const uint64_t cap = uint64_t(st.sms) * uint64_t(occ);
   const uint64_t need = (a.nvec + uint64_t(U) * T - 1) / (uint64_t(U) * T);
   uint64_t grid = std::max<uint64_t>(1, std::min(cap, need));

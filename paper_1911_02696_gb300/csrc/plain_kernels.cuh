@@ -348,11 +348,8 @@ __global__ void __launch_bounds__(NTHREADS) csa64_kernel(PlainArgs a) {
 // Host launcher for width K.
 
 template <typename Kern>
-static int occupancy(Kern kern, int threads, size_t smem) {
-  int blocks = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, threads, smem) != cudaSuccess)
-    return 1;
-  return blocks > 0 ? blocks : 1;
+static int occupancy(const DeviceState& st, Kern kern, int threads, size_t smem) {
+  return resident_blocks(reinterpret_cast<const void*>(kern), st.device, threads, smem);
 }
 
 // Smallest grid whose per-thread, per-warp and per-block u32 partial counts
@@ -387,7 +384,7 @@ static int prepare_counts(PlainArgs& a, uint64_t grid, bool zero_first, cudaStre
 template <int K, int U, int T, bool SYSMEM = false>
 static int launch_csa(const DeviceState& st, PlainArgs a, int bps, bool zero_first, cudaStream_t stream) {
   auto kern = csa_kernel<K, U, T, SYSMEM>;
-  const int occ = occupancy(kern, T, 0);
+  const int occ = occupancy(st, kern, T, 0);
   const uint64_t cap = uint64_t(st.sms) * uint64_t(std::min(bps > 0 ? bps : occ, occ));
   const uint64_t need = (a.nvec + uint64_t(U) * T - 1) / (uint64_t(U) * T);
   uint64_t grid = std::max<uint64_t>(1, std::min(cap, need));
@@ -402,7 +399,7 @@ static int launch_csa(const DeviceState& st, PlainArgs a, int bps, bool zero_fir
 template <int K, int U, int T>
 static int launch_ballot(const DeviceState& st, PlainArgs a, int bps, bool zero_first, cudaStream_t stream) {
   auto kern = ballot_kernel<K, U, T>;
-  const int occ = occupancy(kern, T, 0);
+  const int occ = occupancy(st, kern, T, 0);
   const uint64_t cap = uint64_t(st.sms) * uint64_t(std::min(bps > 0 ? bps : occ, occ));
   const uint64_t per = uint64_t(32) * U * (T / 32);
   const uint64_t need = (a.nvec + per - 1) / per;
@@ -428,7 +425,7 @@ static int launch_tma(const DeviceState& st, const PlainArgs& p, int bps, int st
   a.chunk_bytes = uint32_t(chunk);
   a.stages = uint32_t(stages);
   a.evict_first = (flags & POSPOPCNT_FLAG_EVICT_FIRST) ? 1u : 0u;
-  const int occ = occupancy(kern, TMA_THREADS, smem);
+  const int occ = occupancy(st, kern, TMA_THREADS, smem);
   const uint64_t cap = uint64_t(st.sms) * uint64_t(std::min(bps > 0 ? bps : occ, occ));
   const uint64_t nchunks = (a.body_bytes + chunk - 1) / chunk;
   uint64_t grid = std::max<uint64_t>(1, std::min(cap, nchunks));
@@ -486,7 +483,7 @@ int launch_plain_sysmem_k(const DeviceState& st, const void* d_in, size_t n, uns
 template <int U, int T>
 static int launch_csa64(const DeviceState& st, PlainArgs a, int bps, bool zero_first, cudaStream_t stream) {
   auto kern = csa64_kernel<U, T>;
-  const int occ = occupancy(kern, T, 0);
+  const int occ = occupancy(st, kern, T, 0);
   const uint64_t cap = uint64_t(st.sms) * uint64_t(std::min(bps > 0 ? bps : occ, occ));
   const uint64_t need = (a.nvec + uint64_t(U) * T - 1) / (uint64_t(U) * T);
   uint64_t grid = std::max<uint64_t>(1, std::min(cap, need));
