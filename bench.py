@@ -471,7 +471,8 @@ def run_plain(args, world, rank, local):
         cfg, kname = {"kernel": "onehot", "k": onehot_k}, "onehot"
         lw = 8 if onehot_k <= 8 else 16 if onehot_k <= 16 else 32
         idb = words.itemsize
-        kernel_label = (f"onehot_ring_kernel<{lw}, {idb}>" if nbytes >= (32 << 20) else
+        ring_from = (4 if idb == 1 else 8) << 20  # the library's ring_min_bytes
+        kernel_label = (f"onehot_ring_kernel<{lw}, {idb}>" if nbytes >= ring_from else
                         f"onehot_lut_kernel<{lw}, {idb}, 256>" if idb <= 2 else
                         f"onehot_kernel<{idb}, {lw}, 256>") + f" ({8 * idb}-bit ids, k = {onehot_k})"
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",

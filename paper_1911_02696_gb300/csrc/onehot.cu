@@ -8,11 +8,12 @@
 // bits (the smallest that holds k positions), 32/LW ids share one 32-bit
 // register -- and feeds those registers through the same carry-save circuit
 // and popc flush as the plain count.  Ids >= k encode to the empty word.
-// 32-bit ids are encoded by a clamped shift and a mask (onehot_kernel below
-// 32 MiB: circuit F_4, F_5 for one id per register).  8- and 16-bit ids are
-// encoded by lookups in a table in shared memory (onehot_lut_kernel below
-// 32 MiB).  From 32 MiB every id width goes through onehot_ring_kernel, fed
-// by bulk copies, with the same two encodings; for 8-bit ids and k <= 16 it
+// 32-bit ids are encoded by a clamped shift and a mask (onehot_kernel for
+// small inputs: circuit F_4, F_5 for one id per register).  8- and 16-bit
+// ids are encoded by lookups in a table in shared memory (onehot_lut_kernel
+// for small inputs).  From 4 MiB of 8-bit ids and 8 MiB of wider ids
+// (ring_min_bytes) every id width goes through onehot_ring_kernel, fed by
+// bulk copies, with the same two encodings; for 8-bit ids and k <= 16 it
 // looks up pairs of ids below 16, one lookup for two ids.
 #include <cuda_runtime.h>
 
@@ -697,7 +698,14 @@ struct RingPairs {
 };
 static_assert(RING_CHUNK % (16 * 4 * RING_CWARPS * 32) == 0 && RING_CHUNK % (16 * 2 * RING_CWARPS * 32) == 0,
               "a chunk is a whole number of consumer trips");
-constexpr uint64_t RING_MIN_BYTES = uint64_t(32) << 20;
+// Smallest body (bytes) that takes the bulk-copy kernel: where it overtook
+// the register-load kernels in same-box A/B runs (8-bit ids: behind at 1-2
+// MiB, ahead from 4 MiB for 16 and 32 categories; 16- and 32-bit ids: level
+// or behind at 4 MiB, ahead at 16 MiB).
+template <int IDB>
+constexpr uint64_t ring_min_bytes() {
+  return (IDB == 1 ? uint64_t(4) : uint64_t(8)) << 20;
+}
 
 // The bulk-copy kernel's trip: that of the lookup kernels, except for one
 // 8-bit id per register, where a trip is 4 vectors per thread, 64 ids
@@ -946,7 +954,7 @@ static int launch_onehot(const DeviceState& st, OnehotArgs a, cudaStream_t strea
 
 template <int IDB>
 static int launch_onehot_idb(const DeviceState& st, const OnehotArgs& a, cudaStream_t stream) {
-  if (a.nvec * 16 >= RING_MIN_BYTES) {  // enough chunks to give every SM several
+  if (a.nvec * 16 >= ring_min_bytes<IDB>()) {
     if (a.k <= 8) return launch_onehot_ring<8, IDB>(st, a, stream);
     if (a.k <= 16) return launch_onehot_ring<16, IDB>(st, a, stream);
     return launch_onehot_ring<32, IDB>(st, a, stream);

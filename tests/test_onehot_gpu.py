@@ -2,8 +2,8 @@
 encodes each id and then counts positions, §1): every id width, k on both
 sides of the 8/16/32-bit lane boundaries, ids >= k present, every small
 length at every aligned start, ragged large sizes, skewed ids, both 8-bit-id
-kernels (register loads below 32 MiB, bulk-copy ring above; 32-bit ids
-too), 2 GiB."""
+kernels (register loads below 4 MiB of 8-bit ids or 8 MiB of wider ids,
+bulk-copy ring above; 32-bit ids too), 2 GiB."""
 import numpy as np
 import pytest
 
@@ -74,14 +74,16 @@ def test_u8_every_id_value(k):
 @pytest.mark.parametrize("idb", [1, 2, 4])
 @pytest.mark.parametrize("k", [3, 8, 16, 17, 32])
 def test_bulk_copy_sizes(idb, k):
-    """Ids from 32 MiB up go through bulk copies into a shared-memory ring
-    (8- and 16-bit ids encoded by table lookups, 32-bit ids by shift and
-    mask): the exact threshold, a ragged chunk count, a partial last chunk
-    at an odd start, ids over the whole id range (for 32-bit ids, also ids
-    below 64, most of them counted) and skewed ids."""
+    """Ids from 4 MiB (8-bit) or 8 MiB (16- and 32-bit) up go through bulk
+    copies into a shared-memory ring (8- and 16-bit ids encoded by table
+    lookups, 32-bit ids by shift and mask): the exact threshold and just
+    below it, a ragged chunk count, a partial last chunk at an odd start,
+    ids over the whole id range (for 32-bit ids, also ids below 64, most of
+    them counted) and skewed ids."""
     rng = np.random.default_rng(100 + k + 1000 * idb)
     top = {1: 256, 2: 65536, 4: 1 << 32}[idb]
-    sizes = [(32 << 20, 0), ((32 << 20) - 16, 0), (152 * 32768 * 7 + 16 * 100 + 3, 5), ((40 << 20) + 17, 3)]
+    ring_from = (4 if idb == 1 else 8) << 20
+    sizes = [(ring_from, 0), (ring_from - 16, 0), (152 * 32768 * 7 + 16 * 100 + 3, 5), ((40 << 20) + 17, 3)]
     for nbytes, off in sizes:
         n = nbytes // idb
         ids = rng.integers(0, top, size=n).astype(DT[idb])
@@ -153,8 +155,8 @@ def test_u16_ids_with_high_bytes(k):
 def test_u32_ids_decoys(k):
     """32-bit ids are encoded by a clamped shift: ids of 32 and more (low
     bits a valid category, high bits set, 2^31, 0xFFFFFFFF) must count
-    nowhere, mixed with valid ids, below 32 MiB (register loads) and above
-    (bulk-copy ring)."""
+    nowhere, mixed with valid ids, on both kernels (register loads for the
+    small input, the bulk-copy ring for the two large ones)."""
     rng = np.random.default_rng(11 + k)
     decoys = np.array([32 + j for j in range(32)] + [0x100 + j for j in range(32)] + [0x10000 + j for j in range(32)] +
                       [0xFFFFFFE0 + j for j in range(32)] + [1 << 31, 0xFFFFFFFF], dtype=np.uint32)
@@ -193,7 +195,8 @@ def test_overwrite_on_streams_mixed_with_plain_counts():
     for i, s in enumerate(streams):
         idb = (1, 2, 4, 1, 1, 2)[i]
         k = (32, 17, 16, 9, 32, 5)[i]
-        n = int(rng.integers(1 << 20, (40 << 20) // idb))  # 8-bit ids: both sides of 32 MiB
+        # ids per stream: both kernels of 8- and 16-bit ids, the ring of 32-bit ids
+        n = ((2 << 20) + 5, (3 << 20) + 7, (5 << 20) + 1, (3 << 20) + 11, (24 << 20) + 3, (12 << 20) + 9)[i]
         ids = synth.categorical_ids(200 + i, n, synth.zipf_cdf(min(2 * k, 64)), DT[idb])
         words = synth.uniform_bits(300 + i, int(rng.integers(1 << 20, 6 << 20)), 16)
         wx = torch.from_numpy(words.view(np.uint8)).cuda()
