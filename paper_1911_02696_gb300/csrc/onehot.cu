@@ -338,17 +338,18 @@ __device__ __forceinline__ void flush_mad(uint32_t (&top)[K], uint32_t t, uint32
   for (int p = 0; p < K; ++p) top[p] = mad_one(__popc(t & (lane_mask<K>::value << p)), one, top[p]);
 }
 
-// Per-thread counts of the lookup kernels.  A trip's circuit F_N returns
-// its top register (weight 2^N).  Top registers of consecutive trips are
-// combined as a binary counter of carry-save adders, D levels deep: level j
-// holds at most one pending register of weight 2^(N+j); a second one meets
-// it in a CSA whose sum bit goes to B[N+j] and whose carry (weight
-// 2^(N+j+1)) moves up a level, and the carry out of the last level is
-// flushed with popc.  The flush thus runs once per 2^D trips -- the circuit
-// F_(N+D) without holding 2^(N+D) registers at once.  The register-load
-// kernels take two levels; the bulk-copy kernel with one id per register
-// (LW = 32), whose ALU pipe is filled by the circuit, takes four (flush
-// every 16 trips).
+// Counts of the lookup kernels.  A trip's circuit F_N returns its top
+// register (weight 2^N).  Top registers of consecutive trips are combined
+// as a binary counter of carry-save adders, D levels deep: level j holds at
+// most one pending register of weight 2^(N+j); a second one meets it in a
+// CSA whose sum bit goes to B[N+j] and whose carry (weight 2^(N+j+1)) moves
+// up a level, and the carry out of the last level is flushed.  The flush
+// thus runs once per 2^D trips -- the circuit F_(N+D) without holding
+// 2^(N+D) registers at once.  PairedCounts (the register-load kernels) takes
+// two levels and flushes with popc into LW counters per thread;
+// ColumnCounts (the bulk-copy kernel) flushes through the warp and takes
+// ring_depth levels: four for one id per register (LW = 32), whose ALU pipe
+// is filled by the circuit (flush every 16 trips), two otherwise.
 template <int LW>
 struct ring_depth {
   static constexpr int value = LW == 32 ? 4 : 2;
