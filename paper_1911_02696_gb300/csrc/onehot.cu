@@ -831,7 +831,6 @@ __global__ void __launch_bounds__(RING_THREADS, 1) onehot_ring_kernel(OnehotArgs
   uint8_t* lut = smem;
   const uint8_t* ring = smem + LUT_BYTES;
   RingCtl* ctl = reinterpret_cast<RingCtl*>(smem + LUT_BYTES + size_t(RING_STAGES) * RING_CHUNK);
-  constexpr int N = RingTrip<LW, IDB>::N;
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   const uint64_t body_bytes = a.nvec * 16;
   const uint64_t nchunks = (body_bytes + RING_CHUNK - 1) / RING_CHUNK;
