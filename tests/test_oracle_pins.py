@@ -366,6 +366,59 @@ def test_onehot_counts_table1(golden_dir):
         assert int(c[p]) == freq.get(name, 0)
 
 
+def pin_onehot_high_bits(onehot):
+    """Ids whose low bits name a category but whose high bits are set
+    (256 + j, 0xFF00 + j, 0xFFFF; for 32-bit ids also 0x10000 + j,
+    0xFFFFFFE0 + j, 2^31, 2^32 - 1) are no category below k: only the valid
+    ids are counted, as numpy.bincount counts them."""
+    rng = np.random.default_rng(21)
+    low = [256 + j for j in range(32)] + [0xFF00 + j for j in range(32)] + [0xFFFF]
+    for dt, decoys in ((np.uint16, low),
+                       (np.uint32, low + [0x10000 + j for j in range(32)] + [0xFFFFFFE0 + j for j in range(32)] +
+                        [1 << 31, 0xFFFFFFFF])):
+        for k in (1, 8, 16, 32):
+            valid = rng.integers(0, k, size=3000)
+            ids = np.concatenate([valid, np.repeat(np.array(decoys, dtype=np.int64), 5)]).astype(dt)
+            rng.shuffle(ids)
+            ref = np.bincount(valid, minlength=k)[:k].astype(np.uint64)
+            assert np.array_equal(onehot(ids, k), ref), (dt, k)
+
+
+def test_onehot_counts_ignore_ids_with_high_bits():
+    pin_onehot_high_bits(oracle.onehot_counts)
+
+
+ONEHOT_MUTANTS = {
+    "id_low_byte_only": ("for (int j = 0; j < id_bytes; ++j) v |=", "for (int j = 0; j < 1; ++j) v |="),
+    "id_low_five_bits": ("const uint64_t word = v < (uint64_t)k ?", "v &= 31u;\n    const uint64_t word = v < (uint64_t)k ?"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(ONEHOT_MUTANTS))
+def test_onehot_pin_catches_mutant(name):
+    """A copy of the oracle that reads an id only in part counts decoys; the
+    pin above must fail on it."""
+    src = open(oracle._SRC).read()
+    old, new = ONEHOT_MUTANTS[name]
+    assert src.count(old) == 1, name
+    with tempfile.TemporaryDirectory() as d:
+        cpath, so = os.path.join(d, f"m_{name}.c"), os.path.join(d, f"m_{name}.so")
+        open(cpath, "w").write(src.replace(old, new))
+        subprocess.check_call(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-pthread", cpath, "-o", so])
+        lib = ctypes.CDLL(so)
+        lib.oracle_onehot_counts.restype = ctypes.c_int
+        lib.oracle_onehot_counts.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_void_p]
+
+        def onehot(ids, k):
+            a = np.ascontiguousarray(ids)
+            out = np.zeros(k, dtype=np.uint64)
+            assert lib.oracle_onehot_counts(a.ctypes.data, a.size, a.itemsize, k, out.ctypes.data) == 0
+            return out
+        with pytest.raises(AssertionError):
+            pin_onehot_high_bits(onehot)
+
+
 @pytest.mark.parametrize("dt", [np.uint8, np.uint16, np.uint32])
 def test_onehot_counts_equal_bincount(dt):
     rng = np.random.default_rng(3)
